@@ -1,0 +1,153 @@
+"""ctypes front end of the CPU oracle (``oracle/oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU legs of ``bench.py``; never by the product package.  It does
+argument marshalling only; every step of the arithmetic is in ``oracle.c``.
+The shared object is compiled with gcc on first use (``build()``), in
+``oracle/_build/``, so the same source serves x86 and Arm hosts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+NOT_CONVERGED = -7
+BREAKDOWN = -8
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (plain gcc, no -march)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.oracle_stencil_run.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_int,
+                                           ctypes.c_int, P, P, f64, i64, P, P]
+        lib.oracle_stencil_run.restype = ctypes.c_int
+        lib.oracle_csr_spmv.argtypes = [i32, P, P, P, P, P]
+        lib.oracle_csr_spmv.restype = None
+        lib.oracle_dot.argtypes = [i32, P, P]
+        lib.oracle_dot.restype = f64
+        lib.oracle_cg.argtypes = [i32, P, P, P, P, P, f64, i32, i32, P, P, P, i32]
+        lib.oracle_cg.restype = ctypes.c_int
+        lib.oracle_cg_fp32_ir.argtypes = [i32, P, P, P, P, P, f64, f64, i32, i32, P, P, P]
+        lib.oracle_cg_fp32_ir.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def stencil_run(field: np.ndarray, offsets, weights, steps: int, boundary: float = 0.0,
+                ndim: int | None = None, radius: int | None = None) -> np.ndarray:
+    """Jacobi steps of Eq. (iterativeStencil) on a 1/2/3-D interior array.
+
+    ``field`` has shape (nz, ny, nx) / (ny, nx) / (nx,) (x fastest, C order);
+    ``offsets`` is a sequence of (dx, dy, dz) triples, ``weights`` the matching
+    coefficients.  Returns the field after ``steps`` steps (new array).
+    """
+    lib = _load()
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    nd = f.ndim if ndim is None else ndim
+    dims = list(f.shape[::-1]) + [1, 1, 1]
+    nx, ny, nz = dims[0], dims[1], dims[2]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    if off.shape[0] != w.shape[0]:
+        raise ValueError("offsets and weights differ in length")
+    r = int(np.abs(off).max()) if radius is None else radius
+    out = np.empty_like(f)
+    st = lib.oracle_stencil_run(nd, nx, ny, nz, r, off.shape[0], _ptr(off), _ptr(w),
+                                float(boundary), int(steps), _ptr(f), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_stencil_run failed with status {st}")
+    return out
+
+
+def _csr(rowptr, col, val):
+    return (np.ascontiguousarray(rowptr, dtype=np.int32),
+            np.ascontiguousarray(col, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=np.float64))
+
+
+def spmv(rowptr, col, val, x) -> np.ndarray:
+    lib = _load()
+    rp, c, v = _csr(rowptr, col, val)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    lib.oracle_csr_spmv(n, _ptr(rp), _ptr(c), _ptr(v), _ptr(xx), _ptr(y))
+    return y
+
+
+def dot(u, v) -> float:
+    lib = _load()
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib.oracle_dot(uu.shape[0], _ptr(uu), _ptr(vv)))
+
+
+def cg(rowptr, col, val, b, x0=None, rtol: float = 1e-10, max_iter: int = 10000,
+       max_restarts: int = 4, trace_len: int = 0):
+    """CG of Sec. 2.2.2.  Returns dict(x, status, iters, true_rel, trace)."""
+    lib = _load()
+    rp, c, v = _csr(rowptr, col, val)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    n = rp.shape[0] - 1
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int32(0)
+    tr = ctypes.c_double(0.0)
+    trace = np.zeros((max(trace_len, 1), 3))
+    st = lib.oracle_cg(n, _ptr(rp), _ptr(c), _ptr(v), _ptr(bb), _ptr(x), float(rtol),
+                       int(max_iter), int(max_restarts), ctypes.byref(it), ctypes.byref(tr),
+                       _ptr(trace) if trace_len > 0 else None, int(trace_len))
+    k = min(it.value, trace_len)
+    return dict(x=x, status=st, iters=it.value, true_rel=tr.value, trace=trace[:k].copy())
+
+
+def cg_fp32_ir(rowptr, col, val, b, x0=None, rtol: float = 1e-10, inner_rtol: float = 1e-4,
+               max_inner: int = 5000, max_outer: int = 50):
+    """FP32-inner CG with fp64 iterative refinement.  Returns a dict."""
+    lib = _load()
+    rp, c, v = _csr(rowptr, col, val)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    n = rp.shape[0] - 1
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    inner = ctypes.c_int32(0)
+    outer = ctypes.c_int32(0)
+    tr = ctypes.c_double(0.0)
+    st = lib.oracle_cg_fp32_ir(n, _ptr(rp), _ptr(c), _ptr(v), _ptr(bb), _ptr(x), float(rtol),
+                               float(inner_rtol), int(max_inner), int(max_outer),
+                               ctypes.byref(inner), ctypes.byref(outer), ctypes.byref(tr))
+    return dict(x=x, status=st, inner_iters=inner.value, outer_iters=outer.value,
+                true_rel=tr.value)
