@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the persistent-kernel (PERKS) hot path on GB300.
+
+Workload (one bench step): 3d7pt Jacobi, 384^3 interior cells, fp64, 1000 time
+steps, centre 0.4 / neighbours 0.1, Dirichlet 0, field uniform[0,1) from a
+seed -- one persistent cooperative launch per bench step.  The field (2 x 453
+MB) is larger than L2 (129 MB), so no L2 flush is needed between timed steps.
+
+Printed: ONE JSON line (rank 0) with the contract keys, plus
+  roofline      dominant kernel's achieved algorithmic GB/s vs measured HBM peak;
+  cpu_baseline  the CPU oracle timed on a bounded sample of the same workload;
+  e2e           the same metric through the C ABI with host buffers (H2D + D2H
+                inside the timed region);
+  variants      other configurations of the stencil workload and the CG leg
+                (n = 2^20 synthetic SPD CSR matrix, rtol 1e-10) for context.
+
+``--impl reference`` times the CPU oracle instead (the slow reference arm).
+Multi-GPU (torchrun): every rank runs an independent replica (the workload
+does not shard; no collective on the data path), value = all ranks' cell
+updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stencil GCell-updates/s vs HBM roofline; CG ms to 1e-8 resid (plain vs learned)"
+UNIT = "GCell-updates/s"
+L_3D = 384
+STEPS_3D = 1000
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _loop(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._loop, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for i, n in enumerate(names):
+                if len(s) > 5 + i and s[5 + i].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1):
+    """Times K runs of `steps` Jacobi steps; returns dict with per-run ms."""
+    from paper_2204_02064_gb300 import inputs
+    shape = (L, L, L)
+    f = torch.from_numpy(inputs.stencil_field(shape, seed)).to(
+        {"f64": torch.float64, "f32": torch.float32}[dtype]).cuda()
+    st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
+                     dtype=dtype)
+    desc = st.describe(steps, variant)
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        st.set_field(f)
+        st.run(steps, variant)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(K):
+        st.set_field(f)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.run(steps, variant)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st.check()
+    st.close()
+    return {"ms": times, "desc": desc, "cells": L ** 3}
+
+
+def e2e_leg(api, torch, ctx, L, steps, K, W):
+    """Host-buffer end-to-end: pinned H2D + persistent run + D2H, per step."""
+    from paper_2204_02064_gb300 import inputs
+    shape = (L, L, L)
+    host_in = torch.from_numpy(inputs.stencil_field(shape, 1)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        st.set_field(host_in, stream)
+        st.run(steps, 0, stream)
+        st.get_field(host_out, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        st.set_field(host_in, stream)
+        st.run(steps, 0, stream)
+        st.get_field(host_out, stream)
+    e1.record(stream)
+    e1.synchronize()
+    st.check()
+    ms = e0.elapsed_time(e1) / K
+    nbytes = host_in.numel() * 8
+    st.close()
+    return ms, nbytes, nbytes
+
+
+def cg_leg(api, torch, ctx, K):
+    from paper_2204_02064_gb300 import inputs
+    n = 1 << 20
+    rp, c, v = inputs.csr_spd_matrix(n, inputs.SEED_CG)
+    b = torch.from_numpy(inputs.cg_rhs(n, inputs.SEED_CG)).cuda()
+    op = api.CsrOperator(ctx, torch.from_numpy(rp).cuda(), torch.from_numpy(c).cuda(),
+                         torch.from_numpy(v).cuda())
+    out = {"n": n, "nnz": int(c.shape[0]), "rtol": 1e-10}
+    stream = torch.cuda.current_stream()
+    for mode, name in ((api.CG_FP64, "fp64"), (api.CG_FP32_IR, "fp32_ir"),
+                       (api.CG_FP64_MULTI, "fp64_multi_launch")):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        try:
+            op.solve(b, x, rtol=1e-10, mode=mode)     # warm-up
+            times, stats = [], None
+            for _ in range(K):
+                x.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                op.solve(b, x, rtol=1e-10, mode=mode, stats=False)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                stats = op.last_result()
+            out[name] = {"ms_to_tol": min(times), "iters": stats["iterations"],
+                         "outer": stats["outer_iterations"],
+                         "true_rel_residual": stats["true_rel_residual"],
+                         "sustained_gbs": stats["bytes_per_iteration"] * stats["iterations"]
+                         / (min(times) * 1e-3) / 1e9}
+        except Exception as e:  # report, do not hide
+            out[name] = {"error": str(e)}
+    op.close()
+    return out
+
+
+def cpu_baseline_sample(max_seconds=15.0):
+    """The oracle on a bounded sample of the workload: the 384^3 3d7pt field
+    for as many whole steps as fit in ~max_seconds (at least one)."""
+    from oracle import oracle
+    from paper_2204_02064_gb300 import inputs
+    f = inputs.stencil_field((L_3D, L_3D, L_3D), 1)
+    offs = inputs.shape_offsets("3d7pt")
+    w = inputs.workload_weights("3d7pt")
+    t0 = time.perf_counter()
+    oracle.stencil_run(f, offs, w, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(int(max_seconds / max(t1, 1e-3)), 20))
+    t0 = time.perf_counter()
+    oracle.stencil_run(f, offs, w, steps)
+    dt = time.perf_counter() - t0
+    return {"value": f.size * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"3d7pt fp64 {L_3D}^3 for {steps} steps (of {STEPS_3D}), single-threaded C"}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_2204_02064_gb300 import inputs
+    f = inputs.stencil_field((L_3D, L_3D, L_3D), 1)
+    offs = inputs.shape_offsets("3d7pt")
+    w = inputs.workload_weights("3d7pt")
+    for _ in range(args.warmup):
+        oracle.stencil_run(f, offs, w, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.stencil_run(f, offs, w, 1)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = f.size * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3d7pt Jacobi {L_3D}^3 fp64, Dirichlet 0; CPU oracle, "
+                                   f"each step one Jacobi step of the {STEPS_3D}-step workload",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one Jacobi step of {L_3D}^3 per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-variants", action="store_true", help="only the headline workload")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2204_02064_gb300 import api
+    ctx = api.Context(local)
+    info = ctx.info()
+    peak, peak_kind = _peaks()
+
+    # ---- headline: persistent 3d7pt 384^3 fp64, 1000 steps per bench step
+    from paper_2204_02064_gb300 import inputs
+    shape = (L_3D, L_3D, L_3D)
+    f = torch.from_numpy(inputs.stencil_field(shape, 1)).cuda()
+    st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+    desc = st.describe(STEPS_3D, api.PERSISTENT)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        st.set_field(f)
+        st.run(STEPS_3D)
+    torch.cuda.synchronize()
+    st.set_field(f)
+    per_run = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            st.run(STEPS_3D)
+            evs[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+    st.check()
+    total_ms = t_start.elapsed_time(t_end)
+    per_run = [a.elapsed_time(b) for a, b in evs]
+    total_ms = _max_over_ranks(world, total_ms)
+    cells = float(L_3D ** 3) * STEPS_3D
+    value = world * cells * args.steps / (total_ms * 1e-3) / 1e9
+    mean_launch_ms = sum(per_run) / len(per_run)
+    achieved = desc["algorithmic_bytes"] / (mean_launch_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("kernel_signature") == desc_signature(desc):
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            pass
+    st.close()
+    del f
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        try:
+            ps = stencil_leg(api, torch, ctx, L_3D, STEPS_3D, "f64", api.PER_STEP, 2, 1)
+            variants["3d7pt_384_f64_per_step_baseline"] = {
+                "gcells": cells / (min(ps["ms"]) * 1e-3) / 1e9, "ms": min(ps["ms"])}
+            for L, dt in ((192, "f64"), (192, "f32"), (384, "f32")):
+                for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
+                    r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, var, 2, 1)
+                    c = float(L ** 3) * STEPS_3D
+                    d = r["desc"]
+                    ms = min(r["ms"])
+                    variants[f"3d7pt_{L}_{dt}_{vname}"] = {
+                        "gcells": c / (ms * 1e-3) / 1e9, "ms": ms,
+                        "algorithmic_gbs": d["algorithmic_bytes"] / (ms * 1e-3) / 1e9,
+                        "cached_fraction": d["cached_cells"] / max(d["cells"], 1)}
+        except Exception as e:
+            variants["stencil_error"] = str(e)
+        try:
+            variants["cg"] = cg_leg(api, torch, ctx, 2)
+        except Exception as e:
+            variants["cg"] = {"error": str(e)}
+
+    e2e_ms, h2d, d2h = e2e_leg(api, torch, ctx, L_3D, STEPS_3D, max(1, min(args.steps, 3)), 1)
+    e2e_ms = _max_over_ranks(world, e2e_ms)
+    e2e_val = world * cells / (e2e_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"3d7pt Jacobi {L_3D}^3 fp64, {STEPS_3D} steps per bench "
+                                   "step, centre 0.4 / neighbours 0.1, Dirichlet 0, "
+                                   "uniform[0,1) seeded; one persistent cooperative launch",
+                       "l2": "inputs larger than L2 (2 x 453 MB ping-pong)",
+                       "parallelism": f"replicas x{world}",
+                       "plan": {k: desc[k] for k in ("grid_blocks", "threads_per_block", "tiles_x",
+                                                    "tiles_y", "tiles_z", "reg_cache_planes",
+                                                    "smem_cache_planes", "cached_cells",
+                                                    "halo_cells_per_step")}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "kernel": "perks_stencil_kernel<double, 3d7pt>",
+                         "algorithmic_bytes_per_launch": desc["algorithmic_bytes"],
+                         "mean_launch_ms": mean_launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "device": info,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def desc_signature(desc):
+    return "{grid_blocks}-{threads_per_block}-{tiles_x}x{tiles_y}x{tiles_z}-r{reg_cache_planes}-s{smem_cache_planes}".format(**desc)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

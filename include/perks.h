@@ -1,0 +1,239 @@
+/*
+ * perks.h -- C ABI of the GB300 (sm_103a) persistent-kernel solver library.
+ *
+ * The library implements the PERKS execution model of arXiv 2204.02064
+ * ("PERKS: a Locality-Optimized Execution Model for Iterative Memory-bound
+ * GPU Applications", Sec. 3-4): the time/iteration loop of an iterative
+ * memory-bound solver runs inside ONE cooperative kernel launch with a
+ * device-wide barrier per step, and every thread block keeps its tile of the
+ * state in registers and shared memory between steps, so that only halos and
+ * the uncached remainder travel through L2/HBM.
+ *
+ * Two solvers are exposed:
+ *   - Jacobi stencils (Eq. iterativeStencil, Sec. 2.2.1; Sec. 4.2):
+ *     y(c) = sum_o w_o x(c + o) over 2-D / 3-D grids with a fixed Dirichlet
+ *     boundary, run for N steps;
+ *   - conjugate gradient (Sec. 2.2.2; Sec. 4.3) on a CSR matrix, with the
+ *     merge-path SpMV, dot products and axpys fused into the same persistent
+ *     loop, solved to a relative residual tolerance.
+ *
+ * Conventions (all entry points):
+ *   - Return value: perks_status, 0 on success, a negative PERKS_ERR_* code on
+ *     failure.  No exception, abort or exit crosses the ABI.  A human-readable
+ *     message for the last failure is kept per context (perks_last_error).
+ *   - Pointers: "host" pointers are ordinary CPU memory (pinned or pageable);
+ *     "device" pointers are CUDA global memory of the context's device (for
+ *     example torch.Tensor.data_ptr()).  Each call that takes a buffer says
+ *     which, or takes an on_device flag.
+ *   - Ownership: the library copies every input into device memory it owns
+ *     and frees it in the matching *_destroy.  Caller buffers passed to a
+ *     stream-ordered call must stay valid until that stream reaches the call.
+ *   - Streams: `perks_stream` is a cudaStream_t (NULL = legacy default
+ *     stream).  Calls are stream-ordered; run/solve return before the GPU
+ *     finishes unless they are asked for statistics, in which case they
+ *     synchronize the stream and report device-side errors.
+ *   - Threading: a context and the objects made from it must not be used by
+ *     two host threads at the same time.
+ *   - Layout: grids are row-major with x fastest: element (x, y, z) of an
+ *     nx*ny*nz grid is at index x + nx*(y + ny*z); a 2-D grid is nx*ny.
+ */
+#ifndef PERKS_H
+#define PERKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int perks_status;
+
+#define PERKS_OK 0
+#define PERKS_ERR_INVALID_ARG (-1)       /* a NULL, size or descriptor error */
+#define PERKS_ERR_UNSUPPORTED (-2)       /* valid request the library does not implement */
+#define PERKS_ERR_OUT_OF_MEMORY (-3)     /* a device allocation failed */
+#define PERKS_ERR_LAUNCH_TOO_LARGE (-4)  /* grid not co-resident (Sec. 4.4.1: no oversubscription) */
+#define PERKS_ERR_CUDA (-5)              /* any other CUDA runtime error */
+#define PERKS_ERR_BARRIER_TIMEOUT (-6)   /* a grid barrier wait ran past its limit */
+#define PERKS_ERR_NOT_CONVERGED (-7)     /* CG hit max_iter above tolerance */
+#define PERKS_ERR_BREAKDOWN (-8)         /* CG: <p, Ap> <= 0 or not finite */
+
+typedef struct perks_context perks_context;
+typedef struct perks_stencil perks_stencil;
+typedef struct perks_op perks_op;
+typedef void *perks_stream; /* cudaStream_t */
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (queries SM count, shared memory
+ * and co-residency limits).  *out receives the handle; free it with
+ * perks_context_destroy.  Errors: INVALID_ARG (out NULL or bad device),
+ * CUDA. */
+perks_status perks_context_create(int device, perks_context **out);
+perks_status perks_context_destroy(perks_context *ctx);
+
+/* Message of the last failed call on this context (or on an object made
+ * from it).  Owned by the context; valid until its next call.  Never NULL. */
+const char *perks_last_error(const perks_context *ctx);
+
+/* Limit, in nanoseconds, of every grid-barrier wait inside persistent
+ * kernels launched from this context (default 2e9).  A wait that runs past
+ * it makes the kernel stop all blocks cleanly and the run/solve report
+ * BARRIER_TIMEOUT; 0 makes every wait give up at once (used to test the
+ * error path).  Errors: INVALID_ARG (ctx NULL or limit < 0). */
+perks_status perks_context_set_barrier_timeout(perks_context *ctx, int64_t limit_ns);
+
+/* Device facts used by planners and reports: SM count, opt-in shared memory
+ * per block (bytes), L2 size (bytes).  Any out pointer may be NULL. */
+perks_status perks_context_info(const perks_context *ctx, int32_t *sm_count,
+                                int32_t *smem_per_block, int64_t *l2_bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi stencils: Eq. (iterativeStencil), Sec. 2.2.1; PERKS port, Sec. 4.2 */
+/* ------------------------------------------------------------------------ */
+
+#define PERKS_MAX_POINTS 125
+
+enum { PERKS_F64 = 0, PERKS_F32 = 1, PERKS_BF16 = 2 };
+enum { PERKS_PERSISTENT = 0, PERKS_PER_STEP = 1 };
+
+typedef struct {
+    int32_t ndim;                       /* 2 or 3 */
+    int64_t nx, ny, nz;                 /* interior extents; nz must be 1 when ndim == 2 */
+    int32_t radius;                     /* 1 or 2: ghost ring width, max |offset| */
+    int32_t npts;                       /* number of (offset, weight) pairs, 1..PERKS_MAX_POINTS */
+    int32_t offsets[3 * PERKS_MAX_POINTS]; /* (dx, dy, dz) per point; dz = 0 in 2-D */
+    double weights[PERKS_MAX_POINTS];   /* w_o, applied in the storage dtype's accumulator */
+    int32_t dtype;                      /* PERKS_F64, PERKS_F32 (fp32 accumulate), PERKS_BF16 (fp32 accumulate) */
+    double boundary;                    /* Dirichlet value of every cell outside the interior */
+} perks_stencil_desc;
+
+/* Optional plan override for the persistent kernel (all zero = automatic).
+ * Tile counts split each axis into nearly equal parts, one tile per block. */
+typedef struct {
+    int32_t tiles_x, tiles_y, tiles_z;
+    int32_t smem_cache_planes;          /* -1: as many as fit; >= 0: at most this many */
+    int32_t reg_cache;                  /* 0: no register cache; 1: the compiled register depth */
+    int32_t reserved[4];
+} perks_stencil_plan;
+
+/* What a run did; filled by perks_stencil_run when asked. */
+typedef struct {
+    int64_t steps;
+    int32_t variant;                    /* PERKS_PERSISTENT or PERKS_PER_STEP */
+    int32_t grid_blocks, threads_per_block;
+    int32_t tiles_x, tiles_y, tiles_z;  /* internal orientation: 2-D y maps to z */
+    int32_t reg_cache_planes, smem_cache_planes;
+    int32_t prefetch_planes;
+    int64_t smem_bytes_per_block;
+    int64_t cells;                      /* interior cells */
+    int64_t cached_cells;               /* cells held on chip between steps (D_cache) */
+    int64_t halo_cells_per_step;        /* halo cells written + read per step (H) */
+    double algorithmic_bytes;           /* S (2 N D_uncache + 2 D_cache) + S N H for the whole run */
+} perks_run_stats;
+
+/* Creates a stencil over a device-resident domain described by *desc (the
+ * library keeps its own copy of the field, two ping-pong buffers and the halo
+ * buffers).  Errors: INVALID_ARG (bad extents, radius, offsets outside the
+ * radius, npts), UNSUPPORTED (dtype), OUT_OF_MEMORY. */
+perks_status perks_stencil_create(perks_context *ctx, const perks_stencil_desc *desc,
+                                  perks_stencil **out);
+perks_status perks_stencil_destroy(perks_stencil *st);
+
+/* Plan override (NULL resets to automatic).  Errors: INVALID_ARG,
+ * UNSUPPORTED (the persistent kernel cannot host the requested tiles). */
+perks_status perks_stencil_set_plan(perks_stencil *st, const perks_stencil_plan *plan);
+
+/* Copies nx*ny*nz elements of the storage dtype (double / float / bf16 bits
+ * as uint16) from `src` into the field; `src_on_device` says whether src is a
+ * device (1) or host (0) pointer.  Stream-ordered. */
+perks_status perks_stencil_set_field(perks_stencil *st, const void *src, int src_on_device,
+                                     perks_stream stream);
+
+/* Advances the field by `steps` Jacobi steps (>= 0) with `variant`:
+ *   PERKS_PERSISTENT: one cooperative launch holding the whole time loop
+ *     (Listing 1 / Fig. 4), tiles cached in registers + shared memory,
+ *     halos through L2;
+ *   PERKS_PER_STEP: one launch per step, every step reading and writing the
+ *     whole field in HBM (the baseline PERKS is measured against).
+ * Both give the same values up to rounding order.  With opt_out == NULL the
+ * call is asynchronous; device errors (BARRIER_TIMEOUT) then surface in
+ * perks_stencil_check.  With opt_out != NULL the stream is synchronized and
+ * opt_out filled.  Errors: INVALID_ARG, LAUNCH_TOO_LARGE, UNSUPPORTED,
+ * BARRIER_TIMEOUT, CUDA. */
+perks_status perks_stencil_run(perks_stencil *st, int64_t steps, int32_t variant,
+                               perks_stream stream, perks_run_stats *opt_out);
+
+/* Plans a run without launching it (fills *out as perks_stencil_run would). */
+perks_status perks_stencil_describe(perks_stencil *st, int64_t steps, int32_t variant,
+                                    perks_run_stats *out);
+
+/* Synchronizes `stream` and reports a device-side error of earlier runs on
+ * this stencil (BARRIER_TIMEOUT), clearing it. */
+perks_status perks_stencil_check(perks_stencil *st, perks_stream stream);
+
+/* Copies the current field out (same element type and layout as set_field). */
+perks_status perks_stencil_get_field(perks_stencil *st, void *dst, int dst_on_device,
+                                     perks_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Conjugate gradient: Sec. 2.2.2 (algorithm), Sec. 4.3 (PERKS port)          */
+/* ------------------------------------------------------------------------ */
+
+enum {
+    PERKS_CG_FP64 = 0,        /* fp64 CG, one persistent launch */
+    PERKS_CG_FP32_IR = 1,     /* fp32 inner CG + fp64 true residual and refinement, one launch */
+    PERKS_CG_FP64_MULTI = 2   /* fp64 CG, several launches per iteration (baseline) */
+};
+
+/* Builds a CSR operator with n rows, nnz nonzeros, int32 row pointers
+ * (n+1), int32 column indices (nnz, sorted or not within a row) and fp64
+ * values (nnz).  A must be symmetric positive definite for CG; this is not
+ * checked.  `on_device` says where the three arrays live.  The library keeps
+ * device copies (and an fp32 copy of the values for PERKS_CG_FP32_IR).
+ * Errors: INVALID_ARG (n < 1, nnz < 0, NULL), OUT_OF_MEMORY, CUDA. */
+perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t nnz, const int32_t *rowptr,
+                              const int32_t *col, const double *val, int on_device,
+                              perks_op **out);
+perks_status perks_op_destroy(perks_op *op);
+
+/* y = A x for device vectors of n doubles (merge-path SpMV, one launch). */
+perks_status perks_csr_spmv(perks_op *op, const double *x, double *y, perks_stream stream);
+
+typedef struct {
+    int32_t iterations;          /* CG recurrence iterations (fp32 inner ones for FP32_IR) */
+    int32_t outer_iterations;    /* restarts (FP64) or refinement steps (FP32_IR) */
+    double true_rel_residual;    /* ||b - A x|| / ||b|| in fp64, recomputed on the GPU */
+    int32_t status;              /* same value the call returns */
+    int32_t grid_blocks, threads_per_block;
+    double bytes_per_iteration;  /* algorithmic bytes of one recurrence iteration */
+    double *trace;               /* optional host array of 3*trace_len doubles:
+                                    (alpha_k, beta_k, <r_{k+1}, r_{k+1}>) per iteration */
+    int32_t trace_len;
+} perks_cg_stats;
+
+/* Solves A x = b to ||r|| <= rtol ||b||.  `b` (n doubles) is read, `x` (n
+ * doubles) holds x0 on entry and the solution on exit; both are device
+ * pointers when on_device = 1, host pointers otherwise.  `max_iter` bounds
+ * the recurrence iterations; for FP32_IR `inner_rtol` is the inner solves'
+ * relative tolerance (ignored otherwise).  On exit the true residual is
+ * recomputed in fp64; above tolerance the solver restarts (FP64) or refines
+ * again (FP32_IR) while iterations remain.  With stats == NULL the call is
+ * asynchronous and returns 0 once launched; the outcome is then read by
+ * perks_cg_last_result.  Errors: INVALID_ARG, LAUNCH_TOO_LARGE,
+ * NOT_CONVERGED, BREAKDOWN, BARRIER_TIMEOUT, CUDA. */
+perks_status perks_cg_solve(perks_op *op, const double *b, double *x, double rtol,
+                            int32_t max_iter, int32_t mode, double inner_rtol, int on_device,
+                            perks_stream stream, perks_cg_stats *stats);
+
+/* Synchronizes `stream` and fills *stats (may be NULL) with the outcome of
+ * the last solve; returns that solve's status. */
+perks_status perks_cg_last_result(perks_op *op, perks_stream stream, perks_cg_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERKS_H */

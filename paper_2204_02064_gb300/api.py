@@ -1,0 +1,368 @@
+"""Python binding of the C ABI in include/perks.h (argument marshalling only).
+
+Every step of the solvers runs in libperks_gb300.so; this module converts
+torch tensors / numpy arrays to pointers, passes the current CUDA stream and
+turns status codes into exceptions.  There is no CPU path: if the library is
+missing and cannot be built, importing fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MAX_POINTS = 125
+F64, F32, BF16 = 0, 1, 2
+PERSISTENT, PER_STEP = 0, 1
+CG_FP64, CG_FP32_IR, CG_FP64_MULTI = 0, 1, 2
+
+STATUS = {
+    0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "OUT_OF_MEMORY",
+    -4: "LAUNCH_TOO_LARGE", -5: "CUDA", -6: "BARRIER_TIMEOUT", -7: "NOT_CONVERGED",
+    -8: "BREAKDOWN",
+}
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+
+
+class PerksError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class StencilDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("radius", ctypes.c_int32), ("npts", ctypes.c_int32),
+                ("offsets", ctypes.c_int32 * (3 * MAX_POINTS)),
+                ("weights", ctypes.c_double * MAX_POINTS), ("dtype", ctypes.c_int32),
+                ("boundary", ctypes.c_double)]
+
+
+class StencilPlan(ctypes.Structure):
+    _fields_ = [("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("tiles_z", ctypes.c_int32), ("smem_cache_planes", ctypes.c_int32),
+                ("reg_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("variant", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("tiles_z", ctypes.c_int32), ("reg_cache_planes", ctypes.c_int32),
+                ("smem_cache_planes", ctypes.c_int32), ("prefetch_planes", ctypes.c_int32),
+                ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
+                ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
+                ("algorithmic_bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("bytes_per_iteration", ctypes.c_double),
+                ("trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("trace",)}
+
+
+_lib = None
+_lock = threading.Lock()
+P = ctypes.c_void_p
+
+
+def _declare(lib):
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sigs = {
+        "perks_context_create": ([ctypes.c_int, ctypes.POINTER(P)], i32),
+        "perks_context_destroy": ([P], i32),
+        "perks_last_error": ([P], ctypes.c_char_p),
+        "perks_context_set_barrier_timeout": ([P, i64], i32),
+        "perks_context_info": ([P, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i64)], i32),
+        "perks_stencil_create": ([P, ctypes.POINTER(StencilDesc), ctypes.POINTER(P)], i32),
+        "perks_stencil_destroy": ([P], i32),
+        "perks_stencil_set_plan": ([P, ctypes.POINTER(StencilPlan)], i32),
+        "perks_stencil_set_field": ([P, P, ctypes.c_int, P], i32),
+        "perks_stencil_get_field": ([P, P, ctypes.c_int, P], i32),
+        "perks_stencil_run": ([P, i64, i32, P, ctypes.POINTER(RunStats)], i32),
+        "perks_stencil_describe": ([P, i64, i32, ctypes.POINTER(RunStats)], i32),
+        "perks_stencil_check": ([P, P], i32),
+        "perks_csr_create": ([P, i32, i64, P, P, P, ctypes.c_int, ctypes.POINTER(P)], i32),
+        "perks_op_destroy": ([P], i32),
+        "perks_csr_spmv": ([P, P, P, P], i32),
+        "perks_cg_solve": ([P, P, P, f64, i32, i32, f64, ctypes.c_int, P,
+                            ctypes.POINTER(CgStats)], i32),
+        "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
+    }
+    for name, (args, res) in sigs.items():
+        if not hasattr(lib, name):
+            continue
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libperks_gb300.so, building it with nvcc first if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+        return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return P(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return P(0)
+    if isinstance(stream, int):
+        return P(stream)
+    return P(stream.cuda_stream)
+
+
+def _buffer(obj):
+    """(pointer, on_device, nbytes) of a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(obj, torch.Tensor):
+            if not obj.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return P(obj.data_ptr()), 1 if obj.is_cuda else 0, obj.numel() * obj.element_size()
+    except ImportError:
+        pass
+    if isinstance(obj, np.ndarray):
+        if not obj.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return P(obj.ctypes.data), 0, obj.nbytes
+    raise TypeError(f"unsupported buffer type {type(obj)}")
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = P()
+        st = self._lib.perks_context_create(int(device), ctypes.byref(h))
+        if st != 0:
+            raise PerksError(st, f"perks_context_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+
+    def check(self, st: int):
+        if st != 0:
+            raise PerksError(st, self.last_error)
+
+    @property
+    def last_error(self) -> str:
+        return self._lib.perks_last_error(self.handle).decode()
+
+    def set_barrier_timeout(self, ns: int):
+        self.check(self._lib.perks_context_set_barrier_timeout(self.handle, int(ns)))
+
+    def info(self) -> dict:
+        sm, smem, l2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self.check(self._lib.perks_context_info(self.handle, ctypes.byref(sm), ctypes.byref(smem),
+                                                ctypes.byref(l2)))
+        return {"sm_count": sm.value, "smem_per_block": smem.value, "l2_bytes": l2.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stencil:
+    """A Jacobi stencil over a device-resident grid (perks_stencil_*).
+
+    ``shape`` is (ny, nx) or (nz, ny, nx) in C order (x fastest); ``offsets``
+    are (dx, dy[, dz]) tuples and ``weights`` the matching coefficients.
+    """
+
+    def __init__(self, ctx: Context, shape, offsets, weights, dtype: str = "f64",
+                 boundary: float = 0.0, radius: int | None = None):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        shape = tuple(int(s) for s in shape)
+        if len(shape) not in (2, 3):
+            raise ValueError("shape must be 2-D or 3-D")
+        offs = [tuple(int(v) for v in o) + (0,) * (3 - len(o)) for o in offsets]
+        w = [float(v) for v in weights]
+        if len(offs) != len(w) or not 1 <= len(w) <= MAX_POINTS:
+            raise ValueError("offsets/weights mismatch or too many points")
+        d = StencilDesc()
+        d.ndim = len(shape)
+        dims = shape[::-1] + (1,) * (3 - len(shape))
+        d.nx, d.ny, d.nz = dims
+        d.radius = int(radius if radius is not None else max(max(abs(v) for v in o) for o in offs))
+        d.npts = len(w)
+        for i, o in enumerate(offs):
+            d.offsets[3 * i:3 * i + 3] = list(o)
+            d.weights[i] = w[i]
+        d.dtype = DTYPES[dtype]
+        d.boundary = float(boundary)
+        h = P()
+        ctx.check(self._lib.perks_stencil_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.shape = shape
+        self.dtype = dtype
+        self.cells = int(np.prod(shape))
+
+    def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1):
+        p = StencilPlan()
+        p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
+        p.smem_cache_planes = int(smem_cache_planes)
+        p.reg_cache = int(reg_cache)
+        self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
+
+    def reset_plan(self):
+        self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, None))
+
+    def set_field(self, src, stream=None):
+        ptr, dev, nbytes = _buffer(src)
+        self._check_bytes(nbytes)
+        self.ctx.check(self._lib.perks_stencil_set_field(self.handle, ptr, dev, _stream(stream)))
+
+    def get_field(self, dst, stream=None):
+        ptr, dev, nbytes = _buffer(dst)
+        self._check_bytes(nbytes)
+        self.ctx.check(self._lib.perks_stencil_get_field(self.handle, ptr, dev, _stream(stream)))
+        return dst
+
+    def _check_bytes(self, nbytes):
+        es = {"f64": 8, "f32": 4, "bf16": 2}[self.dtype]
+        if nbytes != self.cells * es:
+            raise ValueError(f"buffer holds {nbytes} bytes, field needs {self.cells * es}")
+
+    def run(self, steps: int, variant: int = PERSISTENT, stream=None, stats: bool = False):
+        if stats:
+            s = RunStats()
+            self.ctx.check(self._lib.perks_stencil_run(self.handle, int(steps), int(variant),
+                                                       _stream(stream), ctypes.byref(s)))
+            return s.as_dict()
+        self.ctx.check(self._lib.perks_stencil_run(self.handle, int(steps), int(variant),
+                                                   _stream(stream), None))
+        return None
+
+    def describe(self, steps: int, variant: int = PERSISTENT) -> dict:
+        s = RunStats()
+        self.ctx.check(self._lib.perks_stencil_describe(self.handle, int(steps), int(variant),
+                                                        ctypes.byref(s)))
+        return s.as_dict()
+
+    def check(self, stream=None):
+        self.ctx.check(self._lib.perks_stencil_check(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_stencil_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CsrOperator:
+    """A CSR matrix on the device (perks_csr_create) and its CG solver."""
+
+    def __init__(self, ctx: Context, rowptr, col, val):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        self._keep = []
+        rp_p, rp_dev, rp_n = _buffer(rowptr)
+        c_p, c_dev, c_n = _buffer(col)
+        v_p, v_dev, v_n = _buffer(val)
+        if not (rp_dev == c_dev == v_dev):
+            raise ValueError("rowptr, col and val must all be host or all device buffers")
+        n = rp_n // 4 - 1
+        nnz = c_n // 4
+        if v_n != 8 * nnz:
+            raise ValueError("val must hold nnz doubles")
+        h = P()
+        ctx.check(self._lib.perks_csr_create(ctx.handle, n, nnz, rp_p, c_p, v_p, rp_dev,
+                                             ctypes.byref(h)))
+        self.handle = h
+        self.n = n
+        self.nnz = nnz
+
+    def spmv(self, x, y, stream=None):
+        xp, xd, _ = _buffer(x)
+        yp, yd, _ = _buffer(y)
+        if not (xd and yd):
+            raise ValueError("spmv takes device vectors")
+        self.ctx.check(self._lib.perks_csr_spmv(self.handle, xp, yp, _stream(stream)))
+
+    def solve(self, b, x, rtol: float = 1e-10, max_iter: int = 10000, mode: int = CG_FP64,
+              inner_rtol: float = 1e-4, stream=None, stats: bool = True, trace_len: int = 0,
+              raise_on_error: bool = True):
+        bp, bd, _ = _buffer(b)
+        xp, xd, _ = _buffer(x)
+        if bd != xd:
+            raise ValueError("b and x must both be host or both device buffers")
+        if not stats:
+            self.ctx.check(self._lib.perks_cg_solve(self.handle, bp, xp, float(rtol), int(max_iter),
+                                                    int(mode), float(inner_rtol), bd,
+                                                    _stream(stream), None))
+            return None
+        s = CgStats()
+        trace = None
+        if trace_len > 0:
+            trace = np.zeros(3 * trace_len)
+            s.trace = trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            s.trace_len = trace_len
+        st = self._lib.perks_cg_solve(self.handle, bp, xp, float(rtol), int(max_iter), int(mode),
+                                      float(inner_rtol), bd, _stream(stream), ctypes.byref(s))
+        out = s.as_dict()
+        out["status_name"] = STATUS.get(st, str(st))
+        if trace is not None:
+            k = min(trace_len, s.iterations)
+            out["trace"] = trace.reshape(-1, 3)[:k].copy()
+        if st != 0 and raise_on_error:
+            raise PerksError(st, self.ctx.last_error)
+        return out
+
+    def last_result(self, stream=None) -> dict:
+        s = CgStats()
+        st = self._lib.perks_cg_last_result(self.handle, _stream(stream), ctypes.byref(s))
+        out = s.as_dict()
+        out["status_name"] = STATUS.get(st, str(st))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,571 @@
+// Host side of the stencil solver: shape matching, the persistent-kernel
+// planner (tile decomposition and register/shared-memory cache split, sized
+// to the device's SMs and shared memory), launches and the C ABI entry
+// points perks_stencil_*.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "stencil_kernels.cuh"
+
+using namespace perks;
+
+namespace {
+
+// ------------------------------------------------------------ shape table
+
+struct ShapeInfo {
+    int ndim, radius;
+    bool box;
+    int npts;
+    const char *name;
+};
+
+template <class SH> ShapeInfo shape_info(const char *name) {
+    return ShapeInfo{SH::NDIM, SH::R, SH::BOX, SH::NPTS, name};
+}
+
+using S2d5 = Shape<2, 1, false>;
+using S3d7 = Shape<3, 1, false>;
+using S2d9 = Shape<2, 1, true>;
+using S2d25 = Shape<2, 2, true>;
+using S2ds9 = Shape<2, 2, false>;
+using S3d27 = Shape<3, 1, true>;
+using S3d13 = Shape<3, 2, false>;
+
+constexpr int kNumShapes = 7;
+
+const ShapeInfo &shape_by_id(int id) {
+    static const ShapeInfo table[kNumShapes] = {
+        shape_info<S2d5>("2d5pt"),   shape_info<S3d7>("3d7pt"),  shape_info<S2d9>("2d9pt"),
+        shape_info<S2d25>("2d25pt"), shape_info<S2ds9>("2ds9pt"), shape_info<S3d27>("3d27pt"),
+        shape_info<S3d13>("3d13pt")};
+    return table[id];
+}
+
+int shape_uoff(int id, int i, int axis) {
+    switch (id) {
+    case 0: return S2d5::uoff(i, axis);
+    case 1: return S3d7::uoff(i, axis);
+    case 2: return S2d9::uoff(i, axis);
+    case 3: return S2d25::uoff(i, axis);
+    case 4: return S2ds9::uoff(i, axis);
+    case 5: return S3d27::uoff(i, axis);
+    default: return S3d13::uoff(i, axis);
+    }
+}
+
+// ------------------------------------------------------- kernel registry
+
+using PersistentFn = void (*)(PersistentArgs);
+
+struct KernelEntry {
+    PersistentFn fn = nullptr;
+    int nt = 0, zr = 0, d = 0;
+    bool configured = false;
+    int smem_budget = 0;  // dynamic shared memory available per block
+};
+
+constexpr int kPrefetch = 4;
+
+template <typename T, class SH, int NT, int ZR>
+KernelEntry entry() {
+    KernelEntry e;
+    e.fn = perks_stencil_kernel<T, SH, NT, ZR, kPrefetch>;
+    e.nt = NT;
+    e.zr = ZR;
+    e.d = kPrefetch;
+    return e;
+}
+
+// [dtype 0=f64,1=f32][shape][reg 0/1]
+KernelEntry &registry(int dtype, int shape, int reg) {
+    static KernelEntry table[2][kNumShapes][2];
+    static bool init = false;
+    if (!init) {
+        init = true;
+        table[0][0][0] = entry<double, S2d5, 256, 0>();
+        table[0][0][1] = entry<double, S2d5, 256, 16>();
+        table[1][0][0] = entry<float, S2d5, 256, 0>();
+        table[1][0][1] = entry<float, S2d5, 256, 16>();
+        table[0][1][0] = entry<double, S3d7, 1024, 0>();
+        table[0][1][1] = entry<double, S3d7, 1024, 8>();
+        table[1][1][0] = entry<float, S3d7, 1024, 0>();
+        table[1][1][1] = entry<float, S3d7, 1024, 8>();
+        table[0][2][0] = entry<double, S2d9, 256, 0>();
+        table[1][2][0] = entry<float, S2d9, 256, 0>();
+        table[0][3][0] = entry<double, S2d25, 256, 0>();
+        table[1][3][0] = entry<float, S2d25, 256, 0>();
+        table[0][4][0] = entry<double, S2ds9, 256, 0>();
+        table[1][4][0] = entry<float, S2ds9, 256, 0>();
+        table[0][5][0] = entry<double, S3d27, 1024, 0>();
+        table[1][5][0] = entry<float, S3d27, 1024, 0>();
+        table[0][6][0] = entry<double, S3d13, 1024, 0>();
+        table[1][6][0] = entry<float, S3d13, 1024, 0>();
+    }
+    return table[dtype][shape][reg];
+}
+
+struct Plan {
+    KernelEntry *k = nullptr;
+    int ntx = 0, nty = 0, ntz = 0;
+    int txmax = 0, tymax = 0, tzmax = 0;
+    int PW = 0, PH = 0, plane = 0, ncol = 0;
+    int zs = 0;
+    long long smem = 0;
+    int blocks = 0;
+    long long cached_cells = 0;
+    long long halo_cells = 0;  // per step
+};
+
+}  // namespace
+
+struct perks_stencil {
+    perks_context *ctx = nullptr;
+    perks_stencil_desc desc{};
+    int es = 8;
+    int X = 0, Y = 0, Z = 0;         // internal orientation (persistent kernel)
+    int uX = 0, uY = 0, uZ = 0;      // user orientation (per-step kernel)
+    long long cells = 0;
+    void *field[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *faces[2] = {nullptr, nullptr};
+    size_t faces_bytes = 0;
+    unsigned long long *bar = nullptr;
+    DevError *err = nullptr;
+    int shape_id = -1;
+    double kw[kMaxKernelPoints] = {};
+    bool has_plan = false;
+    perks_stencil_plan plan{};
+};
+
+namespace {
+
+int match_shape(const perks_stencil_desc &d, double *kw) {
+    for (int id = 0; id < kNumShapes; ++id) {
+        const ShapeInfo &s = shape_by_id(id);
+        if (s.ndim != d.ndim || s.npts != d.npts || s.radius != d.radius) continue;
+        bool ok = true;
+        std::vector<int> used(d.npts, 0);
+        for (int i = 0; i < s.npts && ok; ++i) {
+            int found = -1;
+            for (int j = 0; j < d.npts; ++j) {
+                if (!used[j] && d.offsets[3 * j] == shape_uoff(id, i, 0) &&
+                    d.offsets[3 * j + 1] == shape_uoff(id, i, 1) &&
+                    d.offsets[3 * j + 2] == shape_uoff(id, i, 2)) {
+                    found = j;
+                    break;
+                }
+            }
+            if (found < 0) ok = false;
+            else { used[found] = 1; kw[i] = d.weights[found]; }
+        }
+        if (ok) return id;
+    }
+    return -1;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+perks_status make_plan(perks_stencil *st, Plan &pl) {
+    perks_context *ctx = st->ctx;
+    if (st->shape_id < 0)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                    "persistent kernel: offsets do not match a compiled shape "
+                    "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt)");
+    if (st->desc.dtype == PERKS_BF16)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED, "persistent kernel: BF16 storage is not built yet");
+    const ShapeInfo &sh = shape_by_id(st->shape_id);
+    const int dt = st->desc.dtype == PERKS_F64 ? 0 : 1;
+    int reg = 1;
+    if (st->has_plan) reg = st->plan.reg_cache ? 1 : 0;
+    if (!registry(dt, st->shape_id, reg).fn) reg = 0;
+    KernelEntry &k = registry(dt, st->shape_id, reg);
+    if (!k.configured) {
+        cudaFuncAttributes fa;
+        PERKS_CUDA(ctx, cudaFuncGetAttributes(&fa, (const void *)k.fn));
+        k.smem_budget = ctx->smem_optin - (int)fa.sharedSizeBytes;
+        PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)k.fn,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             k.smem_budget));
+        k.configured = true;
+    }
+    const int R = sh.radius;
+    const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
+    const int S = 2 * RZ + 1 + k.d;
+    const int es = st->es;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, k.nt,
+                                                                  k.smem_budget));
+    if (per_sm < 1)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "persistent kernel cannot be resident");
+    const int maxG = per_sm * ctx->sm_count;
+
+    const int X = st->X, Y = st->Y, Z = st->Z;
+    double best = 1e300;
+    Plan bp;
+    const int fx_lo = st->has_plan && st->plan.tiles_x > 0 ? st->plan.tiles_x : 1;
+    const int fx_hi = st->has_plan && st->plan.tiles_x > 0 ? st->plan.tiles_x : std::min(X, 512);
+    const int fy_lo = st->has_plan && st->plan.tiles_y > 0 ? st->plan.tiles_y : 1;
+    const int fy_hi = st->has_plan && st->plan.tiles_y > 0 ? st->plan.tiles_y : std::min(Y, 512);
+    for (int ntx = fx_lo; ntx <= fx_hi; ++ntx) {
+        const int txmax = ceil_div(X, ntx), txmin = X / ntx;
+        if (txmin < std::max(RX, 1)) break;
+        if (txmax > k.nt) continue;
+        for (int nty = fy_lo; nty <= fy_hi; ++nty) {
+            const int tymax = ceil_div(Y, nty), tymin = Y / nty;
+            if (tymin < std::max(RY, 1)) break;
+            if ((long long)txmax * tymax > k.nt) continue;
+            const int nring = 2 * RY * (txmax + (sh.box ? 2 * RX : 0)) + 2 * RX * tymax;
+            if (nring > k.nt) continue;
+            const int PW = txmax + 2 * RX, PH = tymax + 2 * RY;
+            const long long ring_bytes = (long long)S * PW * PH * es;
+            if (ring_bytes > k.smem_budget) continue;
+            int ntz;
+            if (st->has_plan && st->plan.tiles_z > 0) ntz = st->plan.tiles_z;
+            else ntz = std::min(Z / std::max(RZ, 1), maxG / (ntx * nty));
+            if (ntz < 1 || (long long)ntx * nty * ntz > maxG) continue;
+            if (Z / ntz < std::max(RZ, 1)) continue;
+            const int tzmax = ceil_div(Z, ntz);
+            const double vol = (double)txmax * tymax * tzmax;
+            const double cost = vol * (1.0 + 2.0 * RX / txmax + (RY ? 2.0 * RY / tymax : 0.0) +
+                                       2.0 * RZ / tzmax) +
+                                (txmax < 32 ? vol * 0.25 : 0.0);
+            if (cost < best) {
+                best = cost;
+                bp.ntx = ntx; bp.nty = nty; bp.ntz = ntz;
+                bp.txmax = txmax; bp.tymax = tymax; bp.tzmax = tzmax;
+                bp.PW = PW; bp.PH = PH;
+            }
+        }
+    }
+    if (bp.ntx == 0)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                    "persistent kernel: no tile decomposition of %dx%dx%d fits %d blocks of %d threads",
+                    X, Y, Z, maxG, k.nt);
+    bp.k = &k;
+    bp.plane = bp.PW * bp.PH;
+    bp.ncol = bp.txmax * bp.tymax;
+    bp.blocks = bp.ntx * bp.nty * bp.ntz;
+    const long long ring_bytes = (long long)S * bp.plane * es;
+    long long zs = (k.smem_budget - ring_bytes) / ((long long)bp.ncol * es);
+    zs = std::min<long long>(zs, std::max(0, bp.tzmax - k.zr));
+    if (st->has_plan && st->plan.smem_cache_planes >= 0) zs = std::min<long long>(zs, st->plan.smem_cache_planes);
+    bp.zs = (int)std::max<long long>(0, zs);
+    bp.smem = ring_bytes + (long long)bp.zs * bp.ncol * es;
+
+    // cached cells and halo cells per step, tile by tile
+    long long cached = 0, halo = 0;
+    for (int t = 0; t < bp.blocks; ++t) {
+        const int ti = t % bp.ntx, tj = (t / bp.ntx) % bp.nty, tk = t / (bp.ntx * bp.nty);
+        int x0, tx, y0, ty, z0, tz;
+        split_axis(X, bp.ntx, ti, x0, tx);
+        split_axis(Y, bp.nty, tj, y0, ty);
+        split_axis(Z, bp.ntz, tk, z0, tz);
+        const int zc = std::min(tz, k.zr + bp.zs);
+        cached += (long long)zc * tx * ty;
+        const int nfx = (ti > 0) + (ti + 1 < bp.ntx);
+        const int nfy = (tj > 0) + (tj + 1 < bp.nty);
+        const int nfz = (tk > 0) + (tk + 1 < bp.ntz);
+        // written: x-faces (transposed), y-shell and z-shell of cached planes; read: the same halos
+        const long long wx = (long long)nfx * RX * ty * tz;
+        const long long wy = (long long)nfy * RY * tx * zc;
+        const long long wz = (long long)nfz * RZ * tx * ty;
+        halo += 2 * (wx + wy + wz);
+    }
+    bp.cached_cells = cached;
+    bp.halo_cells = halo;
+    pl = bp;
+    return PERKS_OK;
+}
+
+void fill_stats(const perks_stencil *st, const Plan *pl, long long steps, int variant,
+                perks_run_stats *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->steps = steps;
+    o->variant = variant;
+    o->cells = st->cells;
+    const double S = st->es;
+    if (variant == PERKS_PERSISTENT && pl) {
+        o->grid_blocks = pl->blocks;
+        o->threads_per_block = pl->k->nt;
+        o->tiles_x = pl->ntx; o->tiles_y = pl->nty; o->tiles_z = pl->ntz;
+        o->reg_cache_planes = pl->k->zr;
+        o->smem_cache_planes = pl->zs;
+        o->prefetch_planes = pl->k->d;
+        o->smem_bytes_per_block = pl->smem;
+        o->cached_cells = pl->cached_cells;
+        o->halo_cells_per_step = pl->halo_cells;
+        const double dun = (double)(st->cells - pl->cached_cells);
+        o->algorithmic_bytes = steps > 0 ? S * (2.0 * steps * dun + 2.0 * pl->cached_cells +
+                                                (double)steps * pl->halo_cells) : 0.0;
+    } else {
+        o->threads_per_block = 256;
+        o->algorithmic_bytes = S * 2.0 * (double)steps * (double)st->cells;
+    }
+}
+
+perks_status ensure_persistent_buffers(perks_stencil *st, const Plan &pl) {
+    perks_context *ctx = st->ctx;
+    const int RX = shape_by_id(st->shape_id).radius;
+    const size_t need = (size_t)pl.blocks * 2 * RX * pl.tzmax * pl.tymax * st->es;
+    if (need > st->faces_bytes) {
+        for (int i = 0; i < 2; ++i) {
+            if (st->faces[i]) cudaFree(st->faces[i]);
+            st->faces[i] = nullptr;
+        }
+        st->faces_bytes = 0;
+        for (int i = 0; i < 2; ++i) PERKS_CUDA(ctx, cudaMalloc(&st->faces[i], need));
+        st->faces_bytes = need;
+    }
+    if (!st->bar) PERKS_CUDA(ctx, cudaMalloc(&st->bar, sizeof(unsigned long long)));
+    if (!st->err) PERKS_CUDA(ctx, cudaMalloc(&st->err, sizeof(DevError)));
+    return PERKS_OK;
+}
+
+perks_status read_dev_error(perks_stencil *st, cudaStream_t s) {
+    perks_context *ctx = st->ctx;
+    PERKS_CUDA(ctx, cudaStreamSynchronize(s));
+    if (!st->err) return PERKS_OK;
+    DevError e{};
+    PERKS_CUDA(ctx, cudaMemcpy(&e, st->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e.code != 0) {
+        PERKS_CUDA(ctx, cudaMemset(st->err, 0, sizeof(DevError)));
+        return fail(ctx, e.code, "persistent stencil: grid barrier wait timed out (block %d, barrier %d)",
+                    e.block, e.epoch);
+    }
+    return PERKS_OK;
+}
+
+perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, Plan &pl) {
+    perks_context *ctx = st->ctx;
+    perks_status rc = make_plan(st, pl);
+    if (rc) return rc;
+    rc = ensure_persistent_buffers(st, pl);
+    if (rc) return rc;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)pl.k->fn,
+                                                                  pl.k->nt, pl.smem));
+    if ((long long)per_sm * ctx->sm_count < pl.blocks)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "persistent grid of %d blocks is not co-resident",
+                    pl.blocks);
+    PersistentArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = st->X; a.Y = st->Y; a.Z = st->Z;
+    a.XY = (long long)st->X * st->Y;
+    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
+    a.txmax = pl.txmax; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
+    a.PW = pl.PW; a.plane = pl.plane; a.ncol = pl.ncol;
+    a.zs = pl.zs;
+    a.steps = steps;
+    a.boundary = st->desc.boundary;
+    a.boundary_f = (float)st->desc.boundary;
+    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
+    a.field[0] = st->field[st->cur];
+    a.field[1] = st->field[st->cur ^ 1];
+    a.faces[0] = st->faces[0];
+    a.faces[1] = st->faces[1];
+    a.face_plane = (long long)pl.tzmax * pl.tymax;
+    a.bar = st->bar;
+    a.err = st->err;
+    a.timeout_ns = ctx->timeout_ns;
+    PERKS_CUDA(ctx, cudaMemsetAsync(st->bar, 0, sizeof(unsigned long long), s));
+    PERKS_CUDA(ctx, cudaMemsetAsync(st->err, 0, sizeof(DevError), s));
+    void *args[] = {&a};
+    PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)pl.k->fn, dim3(pl.blocks),
+                                                dim3(pl.k->nt), args, (size_t)pl.smem, s));
+    if (steps & 1) st->cur ^= 1;
+    return PERKS_OK;
+}
+
+template <typename T>
+perks_status launch_steps(perks_stencil *st, long long steps, cudaStream_t s) {
+    perks_context *ctx = st->ctx;
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = st->uX; a.Y = st->uY; a.Z = st->uZ;
+    a.XY = (long long)a.X * a.Y;
+    a.npts = st->desc.npts;
+    a.zchunk = a.Z >= 8 ? 8 : 1;
+    a.boundary = st->desc.boundary;
+    a.boundary_f = (float)st->desc.boundary;
+    for (int i = 0; i < st->desc.npts; ++i) {
+        for (int d = 0; d < 3; ++d) a.off[3 * i + d] = (short)st->desc.offsets[3 * i + d];
+        a.w[i] = st->desc.weights[i];
+        a.wf[i] = (float)st->desc.weights[i];
+    }
+    dim3 block(32, 8);
+    dim3 grid((a.X + 31) / 32, (a.Y + 7) / 8, (a.Z + a.zchunk - 1) / a.zchunk);
+    for (long long k = 0; k < steps; ++k) {
+        const T *in = static_cast<const T *>(st->field[st->cur]);
+        T *out = static_cast<T *>(st->field[st->cur ^ 1]);
+        stencil_step_kernel<T><<<grid, block, 0, s>>>(in, out, a);
+        PERKS_CUDA(ctx, cudaGetLastError());
+        st->cur ^= 1;
+    }
+    return PERKS_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" perks_status perks_stencil_create(perks_context *ctx, const perks_stencil_desc *d,
+                                             perks_stencil **out) {
+    if (!ctx) return PERKS_ERR_INVALID_ARG;
+    if (!d || !out) return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: NULL argument");
+    *out = nullptr;
+    if (d->ndim != 2 && d->ndim != 3)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: ndim must be 2 or 3");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || (d->ndim == 2 && d->nz != 1))
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: bad extents");
+    if (d->nx > INT32_MAX / 2 || d->ny > INT32_MAX / 2 || d->nz > INT32_MAX / 2)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: extent too large");
+    if (d->radius < 1 || d->radius > 2)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: radius must be 1 or 2");
+    if (d->npts < 1 || d->npts > PERKS_MAX_POINTS)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: npts out of range");
+    for (int i = 0; i < d->npts; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const int v = d->offsets[3 * i + a];
+            if (v < -d->radius || v > d->radius || (a == 2 && d->ndim == 2 && v != 0))
+                return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: offset %d outside the radius", i);
+        }
+    if (d->dtype != PERKS_F64 && d->dtype != PERKS_F32 && d->dtype != PERKS_BF16)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED, "stencil_create: unknown dtype %d", d->dtype);
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    perks_stencil *st = new perks_stencil();
+    st->ctx = ctx;
+    st->desc = *d;
+    st->es = (int)dtype_size(d->dtype);
+    st->uX = (int)d->nx; st->uY = (int)d->ny; st->uZ = (int)d->nz;
+    if (d->ndim == 3) { st->X = (int)d->nx; st->Y = (int)d->ny; st->Z = (int)d->nz; }
+    else { st->X = (int)d->nx; st->Y = 1; st->Z = (int)d->ny; }
+    st->cells = (long long)d->nx * d->ny * d->nz;
+    st->shape_id = match_shape(*d, st->kw);
+    const size_t bytes = (size_t)st->cells * st->es;
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = cudaMalloc(&st->field[i], bytes);
+        if (e != cudaSuccess) {
+            perks_stencil_destroy(st);
+            return cuda_fail(ctx, e, "stencil_create: cudaMalloc");
+        }
+    }
+    *out = st;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_destroy(perks_stencil *st) {
+    if (!st) return PERKS_OK;
+    if (st->ctx) cudaSetDevice(st->ctx->device);
+    for (int i = 0; i < 2; ++i) {
+        if (st->field[i]) cudaFree(st->field[i]);
+        if (st->faces[i]) cudaFree(st->faces[i]);
+    }
+    if (st->bar) cudaFree(st->bar);
+    if (st->err) cudaFree(st->err);
+    delete st;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_set_plan(perks_stencil *st, const perks_stencil_plan *plan) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    if (!plan) { st->has_plan = false; return PERKS_OK; }
+    if (plan->tiles_x < 0 || plan->tiles_y < 0 || plan->tiles_z < 0 || plan->smem_cache_planes < -1)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: negative field");
+    st->plan = *plan;
+    st->has_plan = true;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_set_field(perks_stencil *st, const void *src, int src_on_device,
+                                                perks_stream stream) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    if (!src) return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_field: NULL src");
+    perks_status rc = use_device(st->ctx);
+    if (rc) return rc;
+    const size_t bytes = (size_t)st->cells * st->es;
+    PERKS_CUDA(st->ctx, cudaMemcpyAsync(st->field[st->cur], src, bytes,
+                                        src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        (cudaStream_t)stream));
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_get_field(perks_stencil *st, void *dst, int dst_on_device,
+                                                perks_stream stream) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    if (!dst) return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_get_field: NULL dst");
+    perks_status rc = use_device(st->ctx);
+    if (rc) return rc;
+    const size_t bytes = (size_t)st->cells * st->es;
+    PERKS_CUDA(st->ctx, cudaMemcpyAsync(dst, st->field[st->cur], bytes,
+                                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        (cudaStream_t)stream));
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_describe(perks_stencil *st, int64_t steps, int32_t variant,
+                                               perks_run_stats *out) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    if (!out || steps < 0) return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_describe: bad argument");
+    if (variant == PERKS_PERSISTENT) {
+        perks_status rc = use_device(st->ctx);
+        if (rc) return rc;
+        Plan pl;
+        rc = make_plan(st, pl);
+        if (rc) return rc;
+        fill_stats(st, &pl, steps, variant, out);
+    } else if (variant == PERKS_PER_STEP) {
+        fill_stats(st, nullptr, steps, variant, out);
+    } else {
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_describe: unknown variant");
+    }
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_run(perks_stencil *st, int64_t steps, int32_t variant,
+                                          perks_stream stream, perks_run_stats *opt_out) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    perks_context *ctx = st->ctx;
+    if (steps < 0) return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_run: negative steps");
+    if (variant != PERKS_PERSISTENT && variant != PERKS_PER_STEP)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_run: unknown variant %d", variant);
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan pl;
+    bool planned = false;
+    if (steps > 0) {
+        if (variant == PERKS_PERSISTENT) {
+            rc = run_persistent(st, steps, s, pl);
+            planned = true;
+        } else if (st->desc.dtype == PERKS_F64) {
+            rc = launch_steps<double>(st, steps, s);
+        } else if (st->desc.dtype == PERKS_F32) {
+            rc = launch_steps<float>(st, steps, s);
+        } else {
+            rc = launch_steps<__nv_bfloat16>(st, steps, s);
+        }
+        if (rc) return rc;
+    }
+    if (opt_out) {
+        if (variant == PERKS_PERSISTENT && !planned) {
+            rc = make_plan(st, pl);
+            if (rc) return rc;
+        }
+        fill_stats(st, variant == PERKS_PERSISTENT ? &pl : nullptr, steps, variant, opt_out);
+        rc = read_dev_error(st, s);
+        if (rc) return rc;
+    }
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_check(perks_stencil *st, perks_stream stream) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    perks_status rc = use_device(st->ctx);
+    if (rc) return rc;
+    return read_dev_error(st, (cudaStream_t)stream);
+}

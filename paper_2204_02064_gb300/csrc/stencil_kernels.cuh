@@ -1,0 +1,418 @@
+// Jacobi stencil kernels: the persistent (PERKS) kernel and the
+// one-launch-per-step baseline.
+//
+// Method: Eq. (iterativeStencil), Sec. 2.2.1 -- every output cell is a
+// weighted sum of step-k cells at fixed offsets, written out of place -- run
+// as a persistent kernel per Sec. 3 / Sec. 4.2 (Listing 1): the time loop is
+// inside one cooperative launch with a grid barrier per step; each block
+// keeps its tile of the field on chip between steps (a register cache of the
+// first ZR planes of every column and a shared-memory cache of the next zs
+// planes); only halos and the uncached remainder cross L2/HBM.  The vertical
+// (x) edges of each tile are also stored transposed, so that the neighbour
+// reads them as contiguous runs (Sec. 4.2.2).
+//
+// Internal orientation.  Every domain is handled as X*Y*Z with x fastest; a
+// 2-D nx*ny grid becomes X = nx, Y = 1, Z = ny (the streamed axis is the
+// 2-D y axis).  A block owns a tile [x0,x0+tx) x [y0,y0+ty) x [z0,z0+tz)
+// and one thread per (x, y) column of the tile; each thread walks its column
+// along z, one plane per iteration ("each thread computes the cells in a
+// vertical direction", Sec. 4.2.1).
+//
+// Shared memory per block:
+//   ring : S = 2*RZ + 1 + D plane slots, each (tx+2RX) x (ty+2RY) cells: the
+//          planes z-RZ..z+RZ that iteration z reads plus D planes being
+//          prefetched with cp.async (global -> shared staging of halos and of
+//          the uncached interior);
+//   smc  : zs cached planes of the tile's columns (the PERKS shared-memory
+//          cache, updated in place).
+#pragma once
+
+#include "common.cuh"
+
+namespace perks {
+
+constexpr int kMaxKernelPoints = 27;
+
+// Compile-time stencil shape.  Offsets are listed in the user's canonical
+// order (centre, then -x,+x,-y,+y[,-z,+z] per distance for stars; row-major
+// x-fastest for boxes) and mapped to the internal orientation by `off`.
+template <int NDIM_, int R_, bool BOX_> struct Shape {
+    static constexpr int NDIM = NDIM_;
+    static constexpr int R = R_;
+    static constexpr bool BOX = BOX_;
+    static constexpr int W = 2 * R + 1;
+    static constexpr int NPTS = BOX ? (NDIM == 3 ? W * W * W : W * W) : 1 + 2 * NDIM * R;
+    static constexpr int RX = R;
+    static constexpr int RY = NDIM == 3 ? R : 0;
+    static constexpr int RZ = R;
+    // user-orientation offset of point i
+    __host__ __device__ static constexpr int uoff(int i, int axis) {
+        if (BOX) {
+            const int ix = i % W, iy = (i / W) % W, iz = i / (W * W);
+            return axis == 0 ? ix - R : axis == 1 ? iy - R : (NDIM == 3 ? iz - R : 0);
+        }
+        if (i == 0) return 0;
+        const int k = i - 1;
+        const int d = k / (2 * NDIM) + 1;
+        const int a = (k % (2 * NDIM)) / 2;
+        const int s = (k % 2 == 0) ? -1 : 1;
+        return a == axis ? s * d : 0;
+    }
+    // internal-orientation offset (2-D y -> internal z)
+    __host__ __device__ static constexpr int dx(int i) { return uoff(i, 0); }
+    __host__ __device__ static constexpr int dy(int i) { return NDIM == 3 ? uoff(i, 1) : 0; }
+    __host__ __device__ static constexpr int dz(int i) { return NDIM == 3 ? uoff(i, 2) : uoff(i, 1); }
+    static_assert(NPTS <= kMaxKernelPoints, "shape too large for the kernel weight table");
+};
+
+struct PersistentArgs {
+    int X, Y, Z;          // internal interior extents
+    long long XY;
+    int ntx, nty, ntz;    // tile counts per axis (one tile per block)
+    int txmax, tymax, tzmax;
+    int PW, plane;        // ring row pitch and cells per ring slot
+    int ncol;             // txmax*tymax: columns per cached plane
+    int zs;               // shared-memory cache planes
+    long long steps;
+    double boundary;
+    float boundary_f;
+    double w[kMaxKernelPoints];   // weights in the shape's order (fp64 accumulate)
+    float wf[kMaxKernelPoints];   // same, rounded to fp32 (fp32 accumulate)
+    void *field[2];       // ping-pong fields, interior only
+    void *faces[2];       // transposed x-edges, [tile][side][q][z][y]
+    long long face_plane; // tzmax*tymax
+    unsigned long long *bar;
+    DevError *err;
+    long long timeout_ns;
+};
+
+__host__ __device__ inline void split_axis(int n, int parts, int i, int &start, int &len) {
+    const int base = n / parts, rem = n % parts;
+    len = base + (i < rem ? 1 : 0);
+    start = i * base + (i < rem ? i : rem);
+}
+
+template <typename T> __device__ __forceinline__ T bnd_value(const PersistentArgs &a);
+template <> __device__ __forceinline__ double bnd_value<double>(const PersistentArgs &a) { return a.boundary; }
+template <> __device__ __forceinline__ float bnd_value<float>(const PersistentArgs &a) { return a.boundary_f; }
+
+template <typename T> __device__ __forceinline__ typename AccOf<T>::type weight(const PersistentArgs &a, int i);
+template <> __device__ __forceinline__ double weight<double>(const PersistentArgs &a, int i) { return a.w[i]; }
+template <> __device__ __forceinline__ float weight<float>(const PersistentArgs &a, int i) { return a.wf[i]; }
+
+enum RingKind : int { RING_NONE = 0, RING_BOUNDARY = 1, RING_FIELD = 2, RING_FACE = 3 };
+
+// Per-thread state computed once per launch and kept in registers for the
+// whole run (PERKS also caches such intermediate results, Sec. 4.3.2).
+struct ThreadPlan {
+    int tile, x0, y0, z0, tx, ty, tz;
+    bool own;            // this thread owns a column of the tile
+    int lx, ly;
+    long long gxy;       // field offset of the column at z = 0
+    int sidx;            // column's cell within a ring slot
+    bool field_shell;    // column lies within R of a y face that has a neighbour
+    bool has_b, has_t;
+    int wq, eq;          // index of this column in the tile's W / E face (-1: none)
+    int rkind;           // ring cell this thread fills (RingKind)
+    int rsidx;
+    long long rgxy;      // field offset (at z = 0) of the ring cell
+    long long rface;     // face-buffer offset (at z = 0) of the ring cell
+};
+
+template <class SH>
+__device__ __forceinline__ ThreadPlan make_thread_plan(const PersistentArgs &a) {
+    constexpr int RX = SH::RX, RY = SH::RY;
+    ThreadPlan tp;
+    tp.tile = blockIdx.x;
+    const int ti = tp.tile % a.ntx, tj = (tp.tile / a.ntx) % a.nty, tk = tp.tile / (a.ntx * a.nty);
+    split_axis(a.X, a.ntx, ti, tp.x0, tp.tx);
+    split_axis(a.Y, a.nty, tj, tp.y0, tp.ty);
+    split_axis(a.Z, a.ntz, tk, tp.z0, tp.tz);
+    const bool has_w = ti > 0, has_e = ti + 1 < a.ntx;
+    const bool has_s = tj > 0, has_n = tj + 1 < a.nty;
+    tp.has_b = tk > 0;
+    tp.has_t = tk + 1 < a.ntz;
+
+    const int c = threadIdx.x;
+    tp.own = c < tp.tx * tp.ty;
+    tp.lx = tp.own ? c % tp.tx : 0;
+    tp.ly = tp.own ? c / tp.tx : 0;
+    tp.gxy = (long long)(tp.x0 + tp.lx) + (long long)(tp.y0 + tp.ly) * a.X;
+    tp.sidx = (tp.ly + RY) * a.PW + (tp.lx + RX);
+    tp.field_shell = tp.own && ((tp.ly < RY && has_s) || (tp.ly >= tp.ty - RY && has_n));
+    tp.wq = (tp.own && tp.lx < RX && has_w) ? tp.lx : -1;
+    tp.eq = (tp.own && tp.lx >= tp.tx - RX && has_e) ? tp.lx - (tp.tx - RX) : -1;
+
+    // ring cell duty: y-rows first (with corners for box shapes), then x-strips
+    const int wrow = tp.tx + (SH::BOX ? 2 * RX : 0);
+    const int ny_cells = 2 * RY * wrow;
+    const int nx_cells = 2 * RX * tp.ty;
+    tp.rkind = RING_NONE;
+    tp.rsidx = 0;
+    tp.rgxy = 0;
+    tp.rface = 0;
+    int lxr = 0, lyr = 0;
+    bool xstrip = false;
+    int side = 0, q = 0;
+    if (c < ny_cells) {
+        side = c / (RY > 0 ? RY * wrow : 1);
+        q = RY > 0 ? (c / wrow) % RY : 0;
+        lxr = c % wrow - (SH::BOX ? RX : 0);
+        lyr = side == 0 ? -RY + q : tp.ty + q;
+        tp.rkind = RING_FIELD;
+    } else if (c < ny_cells + nx_cells) {
+        const int k = c - ny_cells;
+        side = k / (RX * tp.ty);
+        q = (k / tp.ty) % RX;
+        lyr = k % tp.ty;
+        lxr = side == 0 ? -RX + q : tp.tx + q;
+        xstrip = true;
+        tp.rkind = RING_FACE;
+    }
+    if (tp.rkind != RING_NONE) {
+        const int gx = tp.x0 + lxr, gy = tp.y0 + lyr;
+        tp.rsidx = (lyr + RY) * a.PW + (lxr + RX);
+        if (gx < 0 || gx >= a.X || gy < 0 || gy >= a.Y) {
+            tp.rkind = RING_BOUNDARY;
+        } else {
+            tp.rgxy = (long long)gx + (long long)gy * a.X;
+            if (xstrip) {
+                // W strip = W neighbour's E face (side 1); E strip = E neighbour's W face (side 0)
+                const int nb = side == 0 ? tp.tile - 1 : tp.tile + 1;
+                const int nb_side = side == 0 ? 1 : 0;
+                tp.rface = ((long long)(nb * 2 + nb_side) * RX + q) * a.face_plane + lyr;
+            }
+        }
+    }
+    return tp;
+}
+
+// Fills ring slot `sl` with tile-local plane p of the step's source.
+// REG: p is a compile-time constant here, so regc[p] names a register.
+template <typename T, class SH, int ZR, bool REG>
+__device__ __forceinline__ void fill_plane(const PersistentArgs &a, const ThreadPlan &tp, int p,
+                                           T *sl, const T *fs, const T *hs, const T *smc,
+                                           const T (&regc)[ZR > 0 ? ZR : 1]) {
+    const T bnd = bnd_value<T>(a);
+    const int gz = tp.z0 + p;
+    const bool in_z = gz >= 0 && gz < a.Z;
+    const bool inside = p >= 0 && p < tp.tz;
+    if (tp.own) {
+        T *d = sl + tp.sidx;
+        if (!in_z) {
+            *d = bnd;
+        } else if (!inside) {
+            cp_async<sizeof(T)>(d, fs + (long long)gz * a.XY + tp.gxy);
+        } else {
+            bool done = false;
+            if constexpr (REG && ZR > 0) {
+                if (p >= 0 && p < ZR) { *d = regc[p < 0 ? 0 : (p < ZR ? p : 0)]; done = true; }
+            }
+            if (!done) {
+                if (p < ZR + a.zs) *d = smc[(long long)(p - ZR) * a.ncol + threadIdx.x];
+                else cp_async<sizeof(T)>(d, fs + (long long)gz * a.XY + tp.gxy);
+            }
+        }
+    }
+    if (tp.rkind != RING_NONE) {
+        // star shapes never read the halo ring of planes outside the tile
+        if (inside || SH::BOX) {
+            T *d = sl + tp.rsidx;
+            if (!in_z || tp.rkind == RING_BOUNDARY) {
+                *d = bnd;
+            } else if (tp.rkind == RING_FACE && inside) {
+                cp_async<sizeof(T)>(d, hs + tp.rface + (long long)p * a.tymax);
+            } else {
+                cp_async<sizeof(T)>(d, fs + (long long)gz * a.XY + tp.rgxy);
+            }
+        }
+    }
+}
+
+template <typename T, class SH, int ZR, bool REG>
+__device__ __forceinline__ void store_out(const PersistentArgs &a, const ThreadPlan &tp, int z,
+                                          T v, bool last, T *fd, T *hd, T *smc,
+                                          T (&regc)[ZR > 0 ? ZR : 1]) {
+    constexpr int RX = SH::RX, RZ = SH::RZ;
+    bool cached = false;
+    if constexpr (REG && ZR > 0) {
+        if (z < ZR) { regc[z < ZR ? z : 0] = v; cached = true; }
+    }
+    if (!cached && z < ZR + a.zs) {
+        smc[(long long)(z - ZR) * a.ncol + threadIdx.x] = v;
+        cached = true;
+    }
+    const bool zshell = (z < RZ && tp.has_b) || (z >= tp.tz - RZ && tp.has_t);
+    const long long gz = tp.z0 + z;
+    if (last || !cached || tp.field_shell || zshell) fd[gz * a.XY + tp.gxy] = v;
+    const long long fz = (long long)z * a.tymax + tp.ly;
+    if (tp.wq >= 0) hd[((long long)(tp.tile * 2 + 0) * RX + tp.wq) * a.face_plane + fz] = v;
+    if (tp.eq >= 0) hd[((long long)(tp.tile * 2 + 1) * RX + tp.eq) * a.face_plane + fz] = v;
+}
+
+// One plane iteration: wait for plane z+RZ, compute out(z), store it, start
+// the copy of plane z+RZ+D.  `slo` is the ring slot of plane z-RZ.
+template <typename T, class SH, int ZR, int D, bool REG>
+__device__ __forceinline__ void plane_iteration(const PersistentArgs &a, const ThreadPlan &tp,
+                                                int z, int slo, bool last, T *ring,
+                                                const T *fs, const T *hs, T *fd, T *hd, T *smc,
+                                                T (&regc)[ZR > 0 ? ZR : 1]) {
+    using ACC = typename AccOf<T>::type;
+    constexpr int RZ = SH::RZ;
+    constexpr int S = 2 * RZ + 1 + D;
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    if (tp.own) {
+        ACC acc = ACC(0);
+#pragma unroll
+        for (int i = 0; i < SH::NPTS; ++i) {
+            int s = slo + RZ + SH::dz(i);
+            s = s >= S ? s - S : s;
+            const T *sp = ring + (long long)s * a.plane + tp.sidx + SH::dy(i) * a.PW + SH::dx(i);
+            acc = fma(weight<T>(a, i), to_acc(*sp), acc);
+        }
+        store_out<T, SH, ZR, REG>(a, tp, z, from_acc<T>(acc), last, fd, hd, smc, regc);
+    }
+    const int q = z + RZ + D;
+    if (q < tp.tz + RZ) {
+        int s = slo + 2 * RZ + D;
+        s = s >= S ? s - S : s;
+        fill_plane<T, SH, ZR, REG>(a, tp, q, ring + (long long)s * a.plane, fs, hs, smc, regc);
+    }
+    cp_async_commit();
+}
+
+template <typename T, class SH, int NT, int ZR, int D>
+__global__ void __launch_bounds__(NT, 1) perks_stencil_kernel(const __grid_constant__ PersistentArgs a) {
+    constexpr int RX = SH::RX, RZ = SH::RZ;
+    constexpr int S = 2 * RZ + 1 + D;
+    constexpr int NP_EXTRA = 2 * RZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    T *smc = ring + (long long)S * a.plane;
+    T regc[ZR > 0 ? ZR : 1];
+
+    const ThreadPlan tp = make_thread_plan<SH>(a);
+    unsigned long long epoch = 0;
+
+    // ---- prologue: load the on-chip caches, publish the initial x-edges
+    {
+        const T *f0 = static_cast<const T *>(a.field[0]);
+        T *h0 = static_cast<T *>(a.faces[0]);
+        if (tp.own) {
+#pragma unroll
+            for (int p = 0; p < (ZR > 0 ? ZR : 1); ++p) {
+                if (ZR > 0 && p < tp.tz) regc[p] = f0[(long long)(tp.z0 + p) * a.XY + tp.gxy];
+            }
+            for (int p = ZR; p < tp.tz; ++p) {
+                const bool in_smem = p < ZR + a.zs;
+                if (!in_smem && tp.wq < 0 && tp.eq < 0) break;
+                const T v = f0[(long long)(tp.z0 + p) * a.XY + tp.gxy];
+                if (in_smem) smc[(long long)(p - ZR) * a.ncol + threadIdx.x] = v;
+                const long long fz = (long long)p * a.tymax + tp.ly;
+                if (tp.wq >= 0) h0[((long long)(tp.tile * 2 + 0) * RX + tp.wq) * a.face_plane + fz] = v;
+                if (tp.eq >= 0) h0[((long long)(tp.tile * 2 + 1) * RX + tp.eq) * a.face_plane + fz] = v;
+            }
+            if (tp.wq >= 0 || tp.eq >= 0) {
+#pragma unroll
+                for (int p = 0; p < (ZR > 0 ? ZR : 1); ++p) {
+                    if (ZR > 0 && p < tp.tz) {
+                        const long long fz = (long long)p * a.tymax + tp.ly;
+                        if (tp.wq >= 0) h0[((long long)(tp.tile * 2 + 0) * RX + tp.wq) * a.face_plane + fz] = regc[p];
+                        if (tp.eq >= 0) h0[((long long)(tp.tile * 2 + 1) * RX + tp.eq) * a.face_plane + fz] = regc[p];
+                    }
+                }
+            }
+        }
+    }
+    if (!grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns)) return;
+
+    const int NP = tp.tz + NP_EXTRA;  // planes filled per step
+    int sb = 0;                       // ring slot of plane -RZ in this step
+    for (long long k = 0; k < a.steps; ++k) {
+        const int src = (int)(k & 1);
+        const T *fs = static_cast<const T *>(a.field[src]);
+        const T *hs = static_cast<const T *>(a.faces[src]);
+        T *fd = static_cast<T *>(a.field[src ^ 1]);
+        T *hd = static_cast<T *>(a.faces[src ^ 1]);
+        const bool last = (k + 1 == a.steps);
+
+        // planes -RZ .. RZ+D-1 into slots sb, sb+1, ...
+#pragma unroll
+        for (int j = 0; j < 2 * RZ + D; ++j) {
+            const int p = j - RZ;
+            if (p < tp.tz + RZ) {
+                int s = sb + j;
+                s = s >= S ? s - S : s;
+                fill_plane<T, SH, ZR, true>(a, tp, p, ring + (long long)s * a.plane, fs, hs, smc, regc);
+            }
+            cp_async_commit();
+        }
+        int slo = sb;
+#pragma unroll
+        for (int z = 0; z < ZR; ++z) {
+            if (z < tp.tz) {
+                plane_iteration<T, SH, ZR, D, true>(a, tp, z, slo, last, ring, fs, hs, fd, hd, smc, regc);
+                slo = slo + 1 == S ? 0 : slo + 1;
+            }
+        }
+        for (int z = ZR; z < tp.tz; ++z) {
+            plane_iteration<T, SH, ZR, D, false>(a, tp, z, slo, last, ring, fs, hs, fd, hd, smc, regc);
+            slo = slo + 1 == S ? 0 : slo + 1;
+        }
+        sb = (sb + NP) % S;
+        if (!last) {
+            if (!grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns)) break;
+        }
+    }
+    cp_async_wait_all();
+}
+
+// --------------------------------------------------------------------------
+// One launch per step (baseline).  Generic offsets; every neighbour read goes
+// to L1/L2/HBM; out-of-domain reads take the Dirichlet value.
+// --------------------------------------------------------------------------
+
+constexpr int kMaxStepPoints = PERKS_MAX_POINTS;
+
+struct StepArgs {
+    int X, Y, Z;
+    long long XY;
+    int npts;
+    int zchunk;
+    double boundary;
+    float boundary_f;
+    short off[3 * kMaxStepPoints];  // internal orientation
+    double w[kMaxStepPoints];
+    float wf[kMaxStepPoints];
+};
+
+template <typename T> __device__ __forceinline__ typename AccOf<T>::type step_weight(const StepArgs &a, int i);
+template <> __device__ __forceinline__ double step_weight<double>(const StepArgs &a, int i) { return a.w[i]; }
+template <> __device__ __forceinline__ float step_weight<float>(const StepArgs &a, int i) { return a.wf[i]; }
+template <> __device__ __forceinline__ float step_weight<__nv_bfloat16>(const StepArgs &a, int i) { return a.wf[i]; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) stencil_step_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                           const __grid_constant__ StepArgs a) {
+    using ACC = typename AccOf<T>::type;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.X || y >= a.Y) return;
+    const int zb = blockIdx.z * a.zchunk;
+    const int ze = min(a.Z, zb + a.zchunk);
+    const ACC bnd = sizeof(ACC) == 8 ? (ACC)a.boundary : (ACC)a.boundary_f;
+    for (int z = zb; z < ze; ++z) {
+        ACC acc = ACC(0);
+        for (int i = 0; i < a.npts; ++i) {
+            const int xx = x + a.off[3 * i], yy = y + a.off[3 * i + 1], zz = z + a.off[3 * i + 2];
+            ACC v;
+            if (xx < 0 || xx >= a.X || yy < 0 || yy >= a.Y || zz < 0 || zz >= a.Z) v = bnd;
+            else v = to_acc(__ldg(in + (long long)zz * a.XY + (long long)yy * a.X + xx));
+            acc = fma(step_weight<T>(a, i), v, acc);
+        }
+        out[(long long)z * a.XY + (long long)y * a.X + x] = from_acc<T>(acc);
+    }
+}
+
+}  // namespace perks

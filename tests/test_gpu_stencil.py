@@ -1,0 +1,238 @@
+"""GPU parity of the stencil path (C ABI -> CUDA kernels) against the oracle.
+
+Tolerance (fp64): normwise-per-element relative error
+    max_i |g_i - o_i| / max(|o_i|, 1e-3 * max_j |o_j|) <= 1e-12,
+i.e. relative to the local value floored at 1e-3 of the field maximum (cells
+next to a zero Dirichlet wall decay to tiny values after many contractive
+steps, where a pure elementwise ratio is ill-conditioned).  fp32 storage
+(fp32 accumulation) is compared with the same oracle run in fp64 and must
+stay within 1e-5 for the step counts used here.
+"""
+import numpy as np
+import pytest
+
+from paper_2204_02064_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel_err(g, o):
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    floor = 1e-3 * max(np.max(np.abs(o)), 1e-300)
+    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor)))
+
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+NP = {"f64": np.float64, "f32": np.float32}
+TT = {"f64": torch.float64, "f32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2204_02064_gb300 import api
+    return api.Context(0)
+
+
+def _run_gpu(ctx, name, field, steps, dtype="f64", variant=0, boundary=0.0, plan=None,
+             weights=None, host=False):
+    from paper_2204_02064_gb300 import api
+    offs = inputs.shape_offsets(name)
+    w = inputs.workload_weights(name, seed=5) if weights is None else weights
+    st = api.Stencil(ctx, field.shape, offs, w, dtype=dtype, boundary=boundary)
+    if plan is not None:
+        st.set_plan(**plan)
+    if host:
+        src = np.ascontiguousarray(field.astype(NP[dtype]))
+        st.set_field(src)
+        stats = st.run(steps, variant=variant, stats=True)
+        out = np.empty_like(src)
+        st.get_field(out)
+        torch.cuda.synchronize()
+        return out.astype(np.float64), stats
+    src = torch.from_numpy(field.astype(NP[dtype])).cuda()
+    st.set_field(src)
+    stats = st.run(steps, variant=variant, stats=True)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64), stats
+
+
+def _oracle(oracle, name, field, steps, boundary=0.0, weights=None):
+    w = inputs.workload_weights(name, seed=5) if weights is None else weights
+    return oracle.stencil_run(field, inputs.shape_offsets(name), w, steps, boundary=boundary)
+
+
+CASES = [
+    # (shape name, grid shape, steps)
+    ("2d5pt", (256, 256), 100),        # the 2-D workload at full size
+    ("2d5pt", (157, 203), 37),         # ragged tiles
+    ("2d5pt", (5, 3), 7),              # fewer cells than one tile
+    ("3d7pt", (37, 40, 48), 20),
+    ("3d7pt", (64, 64, 64), 10),
+    ("3d7pt", (3, 4, 5), 4),
+    ("2d9pt", (97, 130), 15),
+    ("2d25pt", (97, 130), 12),
+    ("2ds9pt", (97, 130), 12),
+    ("3d27pt", (29, 33, 40), 6),
+    ("3d13pt", (29, 33, 40), 6),
+]
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["persistent", "per_step"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("name,shape,steps", CASES)
+def test_parity(ctx, oracle, name, shape, steps, dtype, variant):
+    f = inputs.stencil_field(shape, 21)
+    ref = _oracle(oracle, name, f, steps)
+    out, stats = _run_gpu(ctx, name, f, steps, dtype=dtype, variant=variant)
+    assert stats["steps"] == steps
+    assert rel_err(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("plan", [
+    dict(tiles=(3, 2, 2), smem_cache_planes=0, reg_cache=0),     # nothing cached
+    dict(tiles=(3, 2, 2), smem_cache_planes=-1, reg_cache=0),    # shared-memory cache
+    dict(tiles=(3, 2, 2), smem_cache_planes=-1, reg_cache=1),    # registers + shared
+    dict(tiles=(2, 3, 4), smem_cache_planes=3, reg_cache=1),     # partial cache
+    dict(tiles=(1, 2, 1), smem_cache_planes=-1, reg_cache=1),    # one column of blocks
+])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_3d_plans(ctx, oracle, plan, dtype):
+    f = inputs.stencil_field((30, 26, 44), 3)
+    ref = _oracle(oracle, "3d7pt", f, 9)
+    out, stats = _run_gpu(ctx, "3d7pt", f, 9, dtype=dtype, plan=plan)
+    assert stats["tiles_x"] == plan["tiles"][0]
+    assert rel_err(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("plan", [
+    dict(tiles=(4, 1, 6), smem_cache_planes=0, reg_cache=0),
+    dict(tiles=(4, 1, 6), smem_cache_planes=-1, reg_cache=1),
+    dict(tiles=(2, 1, 3), smem_cache_planes=5, reg_cache=1),
+])
+@pytest.mark.parametrize("name", ["2d5pt", "2d25pt", "2d9pt"])
+def test_2d_plans(ctx, oracle, plan, name):
+    f = inputs.stencil_field((90, 70), 4)
+    ref = _oracle(oracle, name, f, 11)
+    out, _ = _run_gpu(ctx, name, f, 11, plan=plan)
+    assert rel_err(out, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_nonzero_boundary_and_host_buffers(ctx, oracle, variant):
+    f = inputs.stencil_field((21, 19, 23), 8)
+    ref = _oracle(oracle, "3d7pt", f, 13, boundary=0.625)
+    out, _ = _run_gpu(ctx, "3d7pt", f, 13, boundary=0.625, variant=variant, host=True)
+    assert rel_err(out, ref) <= 1e-12
+
+
+def test_constant_field_preserved(ctx):
+    f = np.full((40, 36, 52), 0.3)
+    out, _ = _run_gpu(ctx, "3d7pt", f, 50, boundary=0.3)
+    assert np.max(np.abs(out - 0.3)) <= 1e-14
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2])
+def test_few_steps(ctx, oracle, steps):
+    f = inputs.stencil_field((33, 31, 29), 9)
+    out, _ = _run_gpu(ctx, "3d7pt", f, steps)
+    assert rel_err(out, _oracle(oracle, "3d7pt", f, steps)) <= 1e-12
+
+
+def test_composition_bitwise(ctx):
+    from paper_2204_02064_gb300 import api
+    f = torch.from_numpy(inputs.stencil_field((40, 41, 42), 10)).cuda()
+    st = api.Stencil(ctx, f.shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+    st.set_field(f)
+    st.run(7)
+    st.run(6)
+    a = torch.empty_like(f)
+    st.get_field(a)
+    st.set_field(f)
+    st.run(13)
+    b = torch.empty_like(f)
+    st.get_field(b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_persistent_equals_per_step(ctx):
+    f = inputs.stencil_field((48, 50, 64), 12)
+    a, _ = _run_gpu(ctx, "3d7pt", f, 30, variant=0)
+    b, _ = _run_gpu(ctx, "3d7pt", f, 30, variant=1)
+    assert rel_err(a, b) <= 1e-13
+
+
+def test_barrier_timeout_reported_and_context_survives(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    f = inputs.stencil_field((32, 32, 64), 13)
+    ctx.set_barrier_timeout(0)          # every wait gives up at once
+    try:
+        with pytest.raises(api.PerksError) as ei:
+            _run_gpu(ctx, "3d7pt", f, 5, plan=dict(tiles=(2, 2, 2)))
+        assert ei.value.name == "BARRIER_TIMEOUT"
+    finally:
+        ctx.set_barrier_timeout(2_000_000_000)
+    out, _ = _run_gpu(ctx, "3d7pt", f, 5)
+    assert rel_err(out, _oracle(oracle, "3d7pt", f, 5)) <= 1e-12
+
+
+def test_invalid_arguments(ctx):
+    from paper_2204_02064_gb300 import api
+    with pytest.raises(api.PerksError) as ei:
+        api.Stencil(ctx, (8, 8), [(0, 0), (3, 0)], [0.5, 0.5], radius=2)
+    assert ei.value.name == "INVALID_ARG"
+    st = api.Stencil(ctx, (8, 8), inputs.shape_offsets("2d5pt"), [0.2] * 5)
+    with pytest.raises(api.PerksError):
+        st.run(-1)
+    with pytest.raises(api.PerksError):
+        st.run(1, variant=7)
+
+
+def test_unmatched_shape_runs_per_step_only(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    offs = [(0, 0, 0), (1, 0, 0), (0, -1, 0)]
+    w = [0.5, 0.3, 0.2]
+    f = inputs.stencil_field((20, 30), 2)
+    st = api.Stencil(ctx, f.shape, offs, w)
+    with pytest.raises(api.PerksError) as ei:
+        st.run(3, variant=0, stats=True)
+    assert ei.value.name == "UNSUPPORTED"
+    src = torch.from_numpy(f).cuda()
+    st.set_field(src)
+    st.run(3, variant=1)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    ref = oracle.stencil_run(f, offs, w, 3)
+    assert rel_err(out.cpu().numpy(), ref) <= 1e-12
+
+
+# ------------------------------------------------ full-size, closed form
+
+@pytest.mark.parametrize("L,steps,dtype", [(192, 1000, "f64"), (384, 1000, "f64"), (192, 1000, "f32")])
+def test_full_size_sine_mode(ctx, L, steps, dtype):
+    """3d7pt at the bench's sizes: a discrete sine mode decays by its closed-form
+    factor per step, checked on every cell after 1000 steps."""
+    from paper_2204_02064_gb300 import api
+    C, w = 0.4, 0.1
+    k = (1, 1, 2)
+    ang = [kk * np.pi / (L + 1) for kk in k]
+    i = torch.arange(1, L + 1, dtype=torch.float64, device="cuda")
+    u = (torch.sin(ang[2] * i)[:, None, None] * torch.sin(ang[1] * i)[None, :, None]
+         * torch.sin(ang[0] * i)[None, None, :]).contiguous()
+    lam = C + 2 * w * sum(np.cos(t) for t in ang)
+    st = api.Stencil(ctx, u.shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
+                     dtype=dtype)
+    src = u.to(TT[dtype]).contiguous()
+    st.set_field(src)
+    stats = st.run(steps, stats=True)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    ref = (lam ** steps) * u
+    err = ((out.double() - ref).abs().max() / ref.abs().max()).item()
+    assert err <= (1e-11 if dtype == "f64" else 1e-4), (err, stats)
