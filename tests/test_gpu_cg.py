@@ -1,0 +1,201 @@
+"""GPU parity of the CG path (merge-path SpMV + persistent CG) against the oracle.
+
+CG iterates diverge chaotically from any other implementation after many
+steps because the dot products are summed in a different order, so parity is
+checked as:
+  (1) SpMV elementwise (1e-13 relative to the row's absolute sum);
+  (2) alpha_k, beta_k, <r,r>_k of the first 20 iterations within 1e-11 (fp64);
+  (3) iteration counts within +-2 of the oracle's;
+  (4) final x within 1e-7 relative of the oracle's x (rtol 1e-10, kappa ~ 1e2);
+  (5) the true residual, recomputed in fp64, at or below the tolerance on both.
+"""
+import numpy as np
+import pytest
+import scipy.sparse
+
+from paper_2204_02064_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2204_02064_gb300 import api
+    return api.Context(0)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _op(ctx, rp, c, v):
+    from paper_2204_02064_gb300 import api
+    return api.CsrOperator(ctx, _dev(rp), _dev(c), _dev(v))
+
+
+def _rows_abs(rp, c, v, x):
+    A = scipy.sparse.csr_matrix((np.abs(v), c, rp), shape=(len(rp) - 1, len(x)))
+    return A @ np.abs(x)
+
+
+def _spmv_case(ctx, oracle, rp, c, v, seed):
+    n = len(rp) - 1
+    x = inputs.cg_rhs(n, seed)
+    op = _op(ctx, rp, c, v)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    op.spmv(_dev(x), y)
+    torch.cuda.synchronize()
+    ref = oracle.spmv(rp, c, v, x)
+    scale = np.maximum(_rows_abs(rp, c, v, x), 1e-300)
+    assert np.max(np.abs(y.cpu().numpy() - ref) / scale) <= 1e-13
+
+
+@pytest.mark.parametrize("n,seed", [(7, 1), (2000, 2), (50000, 3), (300001, 4)])
+def test_spmv_synthetic(ctx, oracle, n, seed):
+    rp, c, v = inputs.csr_spd_matrix(n, seed)
+    _spmv_case(ctx, oracle, rp, c, v, seed)
+
+
+def test_spmv_long_rows_and_empty_rows(ctx, oracle):
+    """Rows longer than a tile (4096 path items) and empty rows exercise the
+    thread- and tile-level carry fix-up."""
+    rng = np.random.default_rng(5)
+    n = 30000
+    lengths = rng.integers(0, 40, size=n)
+    lengths[::97] = 0
+    lengths[123] = 20000
+    lengths[5000] = 9000
+    lengths[5001] = 4097
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lengths, out=rp[1:])
+    nnz = int(rp[-1])
+    c = rng.integers(0, n, size=nnz).astype(np.int32)
+    v = rng.standard_normal(nnz)
+    _spmv_case(ctx, oracle, rp.astype(np.int32), c, v, 6)
+
+
+@pytest.fixture(scope="module")
+def system_4k():
+    n = 4000
+    rp, c, v = inputs.csr_spd_matrix(n, 31)
+    return rp, c, v, inputs.cg_rhs(n, 31)
+
+
+def _solve(ctx, rp, c, v, b, mode, rtol=1e-10, x0=None, host=False, trace_len=0, **kw):
+    from paper_2204_02064_gb300 import api
+    op = _op(ctx, rp, c, v)
+    n = len(b)
+    if host:
+        x = np.zeros(n) if x0 is None else np.array(x0)
+        res = op.solve(np.ascontiguousarray(b), x, rtol=rtol, mode=mode, trace_len=trace_len, **kw)
+        return x, res
+    x = torch.zeros(n, dtype=torch.float64, device="cuda") if x0 is None else _dev(x0)
+    res = op.solve(_dev(b), x, rtol=rtol, mode=mode, trace_len=trace_len, **kw)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), res
+
+
+@pytest.mark.parametrize("mode", [0, 2], ids=["persistent", "multi_launch"])
+def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode):
+    rp, c, v, b = system_4k
+    ref = oracle.cg(rp, c, v, b, rtol=1e-10, trace_len=20)
+    x, res = _solve(ctx, rp, c, v, b, mode, trace_len=20)
+    tr = res["trace"]
+    assert tr.shape == ref["trace"].shape
+    assert np.max(np.abs(tr - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
+    assert abs(res["iterations"] - ref["iters"]) <= 2
+    assert res["true_rel_residual"] <= 1e-10
+    assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+
+
+def test_cg_fp32_ir(ctx, oracle, system_4k):
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_4k
+    ref = oracle.cg(rp, c, v, b, rtol=1e-10)
+    ir = oracle.cg_fp32_ir(rp, c, v, b, rtol=1e-10, inner_rtol=1e-4)
+    x, res = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, inner_rtol=1e-4)
+    assert res["true_rel_residual"] <= 1e-10
+    assert res["outer_iterations"] >= 2
+    assert abs(res["outer_iterations"] - ir["outer_iters"]) <= 1
+    assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+
+
+def test_cg_host_buffers_and_initial_guess(ctx, oracle, system_4k):
+    rp, c, v, b = system_4k
+    x0 = 0.1 * inputs.cg_rhs(len(b), 77)
+    ref = oracle.cg(rp, c, v, b, x0=x0, rtol=1e-10)
+    x, res = _solve(ctx, rp, c, v, b, 0, x0=x0, host=True)
+    assert res["true_rel_residual"] <= 1e-10
+    assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+
+
+def test_cg_cached_and_streamed_agree(ctx, oracle):
+    # n=2000: every block's slice fits in shared memory (cached A);
+    # n=60000: three or more tiles per block, streamed each iteration.
+    for n in (2000, 60000):
+        rp, c, v = inputs.csr_spd_matrix(n, 8)
+        b = inputs.cg_rhs(n, 8)
+        ref = oracle.cg(rp, c, v, b, rtol=1e-10, trace_len=10)
+        x, res = _solve(ctx, rp, c, v, b, 0, trace_len=10)
+        assert np.max(np.abs(res["trace"] - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
+        assert res["true_rel_residual"] <= 1e-10
+
+
+def test_cg_breakdown_reported(ctx):
+    from paper_2204_02064_gb300 import api
+    A = scipy.sparse.csr_matrix(np.diag([1.0, -1.0]))
+    with pytest.raises(api.PerksError) as ei:
+        _solve(ctx, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data, np.ones(2), 0)
+    assert ei.value.name == "BREAKDOWN"
+
+
+def test_cg_zero_rhs(ctx):
+    rp, c, v = inputs.csr_spd_matrix(100, 1)
+    x, res = _solve(ctx, rp, c, v, np.zeros(100), 0)
+    assert res["iterations"] == 0 and np.all(x == 0)
+
+
+def test_cg_not_converged(ctx, system_4k):
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_4k
+    with pytest.raises(api.PerksError) as ei:
+        _solve(ctx, rp, c, v, b, 0, max_iter=3)
+    assert ei.value.name == "NOT_CONVERGED"
+
+
+def test_cg_barrier_timeout(ctx, system_4k):
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_4k
+    ctx.set_barrier_timeout(0)
+    try:
+        with pytest.raises(api.PerksError) as ei:
+            _solve(ctx, rp, c, v, b, 0)
+        assert ei.value.name == "BARRIER_TIMEOUT"
+    finally:
+        ctx.set_barrier_timeout(2_000_000_000)
+    x, res = _solve(ctx, rp, c, v, b, 0)
+    assert res["true_rel_residual"] <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def system_full():
+    n = 1 << 20
+    rp, c, v = inputs.csr_spd_matrix(n, inputs.SEED_CG)
+    return rp, c, v, inputs.cg_rhs(n, inputs.SEED_CG)
+
+
+def test_cg_full_size(ctx, oracle, system_full):
+    """The CG workload at full size (n = 2^20, rtol 1e-10): trace of the first
+    5 iterations against the oracle, true residual on the GPU side, both
+    modes."""
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_full
+    ref = oracle.cg(rp, c, v, b, rtol=1e-10, max_iter=5, max_restarts=0, trace_len=5)
+    _, res5 = _solve(ctx, rp, c, v, b, 0, max_iter=5, trace_len=5, raise_on_error=False)
+    assert np.max(np.abs(res5["trace"] - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
+    x, res = _solve(ctx, rp, c, v, b, 0)
+    assert res["true_rel_residual"] <= 1e-10
+    x2, res2 = _solve(ctx, rp, c, v, b, api.CG_FP32_IR)
+    assert res2["true_rel_residual"] <= 1e-10
+    assert np.linalg.norm(x - x2) <= 1e-7 * np.linalg.norm(x)
