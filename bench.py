@@ -277,7 +277,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-variants", action="store_true", help="only the headline workload")
+    ap.add_argument("--profile", default=None,
+                    help="run one small case for ncu and exit: stencil3d-f64, stencil3d-f32, "
+                         "stencil3d-f64-perstep, stencil3d-f32-perstep, cg-fp64, cg-fp32ir")
     args = ap.parse_args()
+    if args.profile:
+        return profile_case(args.profile)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -407,6 +412,42 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def profile_case(name):
+    """Small cases for ncu captures: inputs larger than L2 (129 MB) but a few GB
+    on the device at most, one warm-up launch, then the captured launch."""
+    import torch
+    from paper_2204_02064_gb300 import api, inputs
+    ctx = api.Context(0)
+    if name.startswith("stencil3d"):
+        dt = "f64" if "f64" in name else "f32"
+        variant = api.PER_STEP if name.endswith("perstep") else api.PERSISTENT
+        L, steps = 256, (4 if variant == api.PER_STEP else 20)
+        shape = (L, L, L)
+        f = torch.from_numpy(inputs.stencil_field(shape, 1)).to(
+            torch.float64 if dt == "f64" else torch.float32).cuda()
+        st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
+                         dtype=dt)
+        for _ in range(2):
+            st.set_field(f)
+            d = st.run(steps, variant, stats=True)
+        print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d}))
+    elif name.startswith("cg"):
+        n = 1 << 20
+        rp, c, v = inputs.csr_spd_matrix(n, inputs.SEED_CG)
+        op = api.CsrOperator(ctx, torch.from_numpy(rp).cuda(), torch.from_numpy(c).cuda(),
+                             torch.from_numpy(v).cuda())
+        b = torch.from_numpy(inputs.cg_rhs(n, inputs.SEED_CG)).cuda()
+        mode = api.CG_FP32_IR if name == "cg-fp32ir" else api.CG_FP64
+        for _ in range(2):
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            r = op.solve(b, x, rtol=1e-10, mode=mode, max_iter=20, raise_on_error=False)
+        print(json.dumps({"case": name, "n": n, "result": r}))
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    torch.cuda.synchronize()
     return 0
 
 
