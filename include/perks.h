@@ -178,6 +178,38 @@ perks_status perks_stencil_check(perks_stencil *st, perks_stream stream);
 perks_status perks_stencil_get_field(perks_stencil *st, void *dst, int dst_on_device,
                                      perks_stream stream);
 
+/* Allocation-free persistent run, for callers that cannot allocate device
+ * memory: code running under an external memory-pool manager that owns all
+ * device memory, or a latency-critical loop where a cudaMalloc would
+ * synchronize the device.  The paper has no counterpart; this entry point
+ * exists only for such callers.
+ *
+ * Computes what perks_stencil_create + set_field + perks_stencil_run(steps,
+ * PERKS_PERSISTENT) + get_field would, for the stencil *desc (dtype PERKS_F64
+ * or PERKS_F32), without creating a stencil object and without allocating any
+ * memory.  `in` and `out` are device pointers on the calling thread's current
+ * device, each holding nx*ny*nz elements of the dtype; `in` is only read
+ * (in == out updates the field in place; other overlaps are undefined) and
+ * `out` receives the field after `steps` steps.
+ *
+ * Scratch (second ping-pong field, transposed x-edges, barrier counter, error
+ * record) is one static device array compiled into the library, about 12 MiB,
+ * held on every GPU that loads the library until the process exits.  Limits:
+ * nx*ny*nz <= 2^20 cells and the plan's x-edge buffers <= 4 MiB; larger
+ * problems return PERKS_ERR_INVALID_ARG before any GPU work.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call outside any stream capture.  Every call reuses the
+ * same array and clears its counter and error record, so calls whose kernels
+ * overlap on the GPU (other streams, other host threads) race.
+ *
+ * sync == 0: asynchronous, device-side errors are not reported; sync != 0:
+ * synchronizes `stream` and returns PERKS_ERR_BARRIER_TIMEOUT if a grid
+ * barrier wait ran past 2 s.  Other errors: INVALID_ARG, UNSUPPORTED (shape
+ * or dtype without a persistent kernel), LAUNCH_TOO_LARGE, CUDA.  No message
+ * is recorded (there is no context). */
+perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc, const void *in, void *out,
+                                       int64_t steps, perks_stream stream, int32_t sync);
+
 /* ------------------------------------------------------------------------ */
 /* Conjugate gradient: Sec. 2.2.2 (algorithm), Sec. 4.3 (PERKS port)          */
 /* ------------------------------------------------------------------------ */

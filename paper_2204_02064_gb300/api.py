@@ -102,6 +102,7 @@ def _declare(lib):
         "perks_cg_solve": ([P, P, P, f64, i32, i32, f64, ctypes.c_int, P,
                             ctypes.POINTER(CgStats)], i32),
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
+        "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
     }
     for name, (args, res) in sigs.items():
         if not hasattr(lib, name):
@@ -195,6 +196,44 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def _stencil_desc(shape, offsets, weights, dtype, boundary, radius):
+    shape = tuple(int(s) for s in shape)
+    if len(shape) not in (2, 3):
+        raise ValueError("shape must be 2-D or 3-D")
+    offs = [tuple(int(v) for v in o) + (0,) * (3 - len(o)) for o in offsets]
+    w = [float(v) for v in weights]
+    if len(offs) != len(w) or not 1 <= len(w) <= MAX_POINTS:
+        raise ValueError("offsets/weights mismatch or too many points")
+    d = StencilDesc()
+    d.ndim = len(shape)
+    d.nx, d.ny, d.nz = shape[::-1] + (1,) * (3 - len(shape))
+    d.radius = int(radius if radius is not None else max(max(abs(v) for v in o) for o in offs))
+    d.npts = len(w)
+    for i, o in enumerate(offs):
+        d.offsets[3 * i:3 * i + 3] = list(o)
+        d.weights[i] = w[i]
+    d.dtype = DTYPES[dtype]
+    d.boundary = float(boundary)
+    return d
+
+
+def stencil_run_noalloc(shape, offsets, weights, src, dst, steps: int, dtype: str = "f64",
+                        boundary: float = 0.0, radius: int | None = None, stream=None,
+                        sync: bool = True):
+    """perks_stencil_run_noalloc: persistent run from device tensor `src` into
+    device tensor `dst` with no allocation (scratch is a static device array)."""
+    lib = load()
+    d = _stencil_desc(shape, offsets, weights, dtype, boundary, radius)
+    sp, sdev, sn = _buffer(src)
+    dp, ddev, dn = _buffer(dst)
+    if not (sdev and ddev):
+        raise ValueError("src and dst must be device tensors")
+    st = lib.perks_stencil_run_noalloc(ctypes.byref(d), sp, dp, int(steps), _stream(stream),
+                                       1 if sync else 0)
+    if st != 0:
+        raise PerksError(st, "perks_stencil_run_noalloc failed")
 
 
 class Stencil:

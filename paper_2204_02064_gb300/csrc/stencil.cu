@@ -569,3 +569,171 @@ extern "C" perks_status perks_stencil_check(perks_stencil *st, perks_stream stre
     if (rc) return rc;
     return read_dev_error(st, (cudaStream_t)stream);
 }
+
+// ============================================== allocation-free entry point
+//
+// For callers that must not allocate device memory (for example code that
+// runs inside a memory-pool-managed runtime or a real-time loop where a
+// cudaMalloc would block or is forbidden).  The caller supplies the input and
+// output fields; everything else the persistent kernel needs -- the second
+// ping-pong field, the transposed x-edge buffers, the grid-barrier counter
+// and the device error record -- lives in one file-scope __device__ array.
+// That array is part of the library image: every GPU on which the library is
+// loaded keeps it (kNoallocScratchBytes, about 12 MiB) until the process
+// exits.  All calls share it, so calls whose kernels overlap on the GPU
+// (different streams, or several host threads) race and give wrong results;
+// it keeps the last call's contents, and the counter and error record are
+// cleared at the start of every call.
+
+namespace {
+
+constexpr long long kNoallocMaxCells = 1ll << 20;             // second field buffer
+constexpr size_t kNoallocHeaderBytes = 256;                   // barrier counter + error record
+constexpr size_t kNoallocFieldBytes = (size_t)kNoallocMaxCells * 8;
+constexpr size_t kNoallocFaceBytes = (size_t)4 << 20;          // transposed x-edges, both parities
+constexpr size_t kNoallocScratchBytes = kNoallocHeaderBytes + kNoallocFieldBytes + kNoallocFaceBytes;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+cudaError_t noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+// Shape matching with a fixed-size table on the stack (no heap use).
+int match_shape_noalloc(const perks_stencil_desc &d, double *kw) {
+    for (int id = 0; id < kNumShapes; ++id) {
+        const ShapeInfo &s = shape_by_id(id);
+        if (s.ndim != d.ndim || s.npts != d.npts || s.radius != d.radius) continue;
+        unsigned char used[PERKS_MAX_POINTS] = {};
+        bool ok = true;
+        for (int i = 0; i < s.npts && ok; ++i) {
+            int found = -1;
+            for (int j = 0; j < d.npts; ++j)
+                if (!used[j] && d.offsets[3 * j] == shape_uoff(id, i, 0) &&
+                    d.offsets[3 * j + 1] == shape_uoff(id, i, 1) && d.offsets[3 * j + 2] == shape_uoff(id, i, 2)) {
+                    found = j;
+                    break;
+                }
+            if (found < 0) ok = false;
+            else { used[found] = 1; kw[i] = d.weights[found]; }
+        }
+        if (ok) return id;
+    }
+    return -1;
+}
+
+}  // namespace
+
+extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc, const void *in, void *out,
+                                                  int64_t steps, perks_stream stream, int32_t sync) {
+    if (!desc || !in || !out || steps < 0) return PERKS_ERR_INVALID_ARG;
+    const perks_stencil_desc &d = *desc;
+    if ((d.ndim != 2 && d.ndim != 3) || d.nx < 1 || d.ny < 1 || d.nz < 1 || (d.ndim == 2 && d.nz != 1))
+        return PERKS_ERR_INVALID_ARG;
+    if (d.radius < 1 || d.radius > 2 || d.npts < 1 || d.npts > PERKS_MAX_POINTS) return PERKS_ERR_INVALID_ARG;
+    for (int i = 0; i < d.npts; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const int v = d.offsets[3 * i + a];
+            if (v < -d.radius || v > d.radius || (a == 2 && d.ndim == 2 && v != 0)) return PERKS_ERR_INVALID_ARG;
+        }
+    if (d.dtype != PERKS_F64 && d.dtype != PERKS_F32) return PERKS_ERR_UNSUPPORTED;
+    const long long cells = d.nx * d.ny * d.nz;
+    if (cells > kNoallocMaxCells) return PERKS_ERR_INVALID_ARG;  // beyond the scratch field's capacity
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = dtype_size(d.dtype);
+    const size_t bytes = (size_t)cells * es;
+    if (steps == 0) {
+        if (in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return PERKS_ERR_CUDA;
+        return PERKS_OK;
+    }
+
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return PERKS_ERR_CUDA;
+    unsigned char *scratch = nullptr;
+    if (noalloc_scratch(device, &scratch) != cudaSuccess) return PERKS_ERR_CUDA;
+
+    // device facts and a stencil description on the stack: nothing is allocated
+    perks_context ctx;
+    ctx.device = device;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PERKS_ERR_CUDA;
+    ctx.sm_count = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+        return PERKS_ERR_CUDA;
+    ctx.smem_optin = v;
+    perks_stencil st;
+    st.ctx = &ctx;
+    st.desc = d;
+    st.es = (int)es;
+    st.uX = (int)d.nx; st.uY = (int)d.ny; st.uZ = (int)d.nz;
+    if (d.ndim == 3) { st.X = (int)d.nx; st.Y = (int)d.ny; st.Z = (int)d.nz; }
+    else { st.X = (int)d.nx; st.Y = 1; st.Z = (int)d.ny; }
+    st.cells = cells;
+    st.shape_id = match_shape_noalloc(d, st.kw);
+    if (st.shape_id < 0) return PERKS_ERR_UNSUPPORTED;
+    Plan pl;
+    perks_status rc = make_plan(&st, pl);
+    if (rc) return rc;
+    const int RX = shape_by_id(st.shape_id).radius;
+    const size_t face_bytes = (size_t)pl.blocks * 2 * RX * pl.tzmax * pl.tymax * es;
+    if (2 * face_bytes > kNoallocFaceBytes) return PERKS_ERR_INVALID_ARG;  // edges exceed the scratch
+
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(scratch);
+    DevError *err = reinterpret_cast<DevError *>(scratch + 64);
+    void *field2 = scratch + kNoallocHeaderBytes;
+    unsigned char *faces = scratch + kNoallocHeaderBytes + kNoallocFieldBytes;
+
+    PersistentArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = st.X; a.Y = st.Y; a.Z = st.Z;
+    a.XY = (long long)st.X * st.Y;
+    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
+    a.txmax = pl.txmax; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
+    a.PW = pl.PW; a.plane = pl.plane; a.ncol = pl.ncol;
+    a.zs = pl.zs;
+    a.steps = steps;
+    a.boundary = d.boundary;
+    a.boundary_f = (float)d.boundary;
+    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st.kw[i]; a.wf[i] = (float)st.kw[i]; }
+    a.field[0] = out;
+    a.field[1] = field2;
+    a.faces[0] = faces;
+    a.faces[1] = faces + face_bytes;
+    a.face_plane = (long long)pl.tzmax * pl.tymax;
+    a.bar = bar;
+    a.err = err;
+    a.timeout_ns = ctx.timeout_ns;
+
+    if (in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return PERKS_ERR_CUDA;
+    if (cudaMemsetAsync(scratch, 0, kNoallocHeaderBytes, s) != cudaSuccess) return PERKS_ERR_CUDA;
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)pl.k->fn, dim3(pl.blocks), dim3(pl.k->nt), args,
+                                                (size_t)pl.smem, s);
+    if (e == cudaErrorCooperativeLaunchTooLarge) return PERKS_ERR_LAUNCH_TOO_LARGE;
+    if (e != cudaSuccess) return PERKS_ERR_CUDA;
+    if (steps & 1) {  // the last step wrote the scratch field
+        if (cudaMemcpyAsync(out, field2, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return PERKS_ERR_CUDA;
+    }
+    if (sync) {
+        DevError he{};
+        if (cudaMemcpyAsync(&he, err, sizeof(he), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PERKS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PERKS_ERR_CUDA;
+        if (he.code != 0) return he.code;
+    }
+    return PERKS_OK;
+}
