@@ -278,8 +278,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-variants", action="store_true", help="only the headline workload")
     ap.add_argument("--profile", default=None,
-                    help="run one small case for ncu and exit: stencil3d-f64, stencil3d-f32, "
-                         "stencil3d-f64-perstep, stencil3d-f32-perstep, cg-fp64, cg-fp32ir")
+                    help="run one small case for ncu and exit: headline, stencil3d-f64, "
+                         "stencil3d-f32, stencil3d-bf16, stencil3d-f64-perstep, "
+                         "stencil3d-f32-perstep, cg-fp64, cg-fp32ir")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile)
@@ -421,13 +422,27 @@ def profile_case(name):
     import torch
     from paper_2204_02064_gb300 import api, inputs
     ctx = api.Context(0)
-    if name.startswith("stencil3d"):
-        dt = "f64" if "f64" in name else "f32"
+    if name.startswith("headline"):
+        # the bench's own launch configuration (3d7pt fp64 384^3, same plan),
+        # two short launches of 20 and 40 steps: per-launch DRAM traffic is
+        # a + b * steps, so a 1000-step launch is extrapolated from the pair
+        L = L_3D
+        shape = (L, L, L)
+        f = torch.from_numpy(inputs.stencil_field(shape, 1)).cuda()
+        st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+        st.set_field(f)
+        st.run(2, stats=True)                      # warm-up launch (not captured: -s 1)
+        for steps in (20, 40):
+            st.set_field(f)
+            d = st.run(steps, stats=True)
+            print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d}))
+    elif name.startswith("stencil3d"):
+        dt = "f64" if "f64" in name else ("bf16" if "bf16" in name else "f32")
         variant = api.PER_STEP if name.endswith("perstep") else api.PERSISTENT
         L, steps = 256, (4 if variant == api.PER_STEP else 20)
         shape = (L, L, L)
         f = torch.from_numpy(inputs.stencil_field(shape, 1)).to(
-            torch.float64 if dt == "f64" else torch.float32).cuda()
+            {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]).cuda()
         st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
                          dtype=dt)
         for _ in range(2):

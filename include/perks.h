@@ -116,7 +116,8 @@ typedef struct {
     int32_t tiles_x, tiles_y, tiles_z;
     int32_t smem_cache_planes;          /* -1: as many as fit; >= 0: at most this many */
     int32_t reg_cache;                  /* 0: no register cache; 1: the compiled register depth */
-    int32_t reserved[4];
+    int32_t reserved[4];                /* reserved[0] = 1: one-cell-per-thread kernel instead of
+                                           the 16-byte-vector kernel; others must be 0 */
 } perks_stencil_plan;
 
 /* What a run did; filled by perks_stencil_run when asked. */
@@ -211,6 +212,53 @@ perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc, const voi
                                        int64_t steps, perks_stream stream, int32_t sync);
 
 /* ------------------------------------------------------------------------ */
+/* Batched stencils: many uneven 2-D domains in one persistent launch         */
+/* (Sec. 3 execution model applied to a set of domains; tile assignment and  */
+/* cache split from the Sec. 5.2 performance model, refined by timing)       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct perks_batch perks_batch;
+
+typedef struct {
+    int64_t steps;
+    int32_t grid_blocks;
+    int32_t tiles;                      /* tiles over all domains */
+    int32_t max_tiles_per_block;
+    int32_t width_cap;                  /* max tile width in cells (0: kernel limit) */
+    int64_t smem_bytes_per_block;
+    int64_t cells, cached_cells, halo_cells_per_step;
+    double granularity;                 /* target tile cells / (total cells / blocks) */
+    double predicted_ms_per_step;       /* model makespan of the chosen plan */
+    double algorithmic_bytes;           /* S (2 N D_uncache + 2 D_cache) + S N H */
+} perks_batch_stats;
+
+/* Creates a batch of `ndom` 2-D domains, descs[i] each (all the same dtype;
+ * shapes 2d5pt, 2d9pt, 2d25pt or 2ds9pt in any mix; nx a multiple of 16 bytes
+ * of cells: 2 for F64, 4 for F32, 8 for BF16).  The library owns two field
+ * buffers per domain.  Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY. */
+perks_status perks_batch_create(perks_context *ctx, int32_t ndom, const perks_stencil_desc *descs,
+                                perks_batch **out);
+perks_status perks_batch_destroy(perks_batch *b);
+/* Field of domain `dom` in/out (nx*ny elements, layout as perks_stencil_set_field). */
+perks_status perks_batch_set_field(perks_batch *b, int32_t dom, const void *src, int src_on_device,
+                                   perks_stream stream);
+perks_status perks_batch_get_field(perks_batch *b, int32_t dom, void *dst, int dst_on_device,
+                                   perks_stream stream);
+/* Advances every domain by `steps` steps: PERKS_PERSISTENT = one cooperative
+ * launch for all domains; PERKS_PER_STEP = one launch per domain per step
+ * (baseline).  opt_out as in perks_stencil_run. */
+perks_status perks_batch_run(perks_batch *b, int64_t steps, int32_t variant, perks_stream stream,
+                             perks_batch_stats *opt_out);
+/* Autotuner: ranks tile granularities and width caps with the performance
+ * model, times the best few for `probe_steps` steps each (0: model only;
+ * the fields are restored afterwards) and keeps the fastest plan.  Allocates
+ * a temporary copy of the fields while probing.  *chosen may be NULL. */
+perks_status perks_batch_autotune(perks_batch *b, int64_t probe_steps, perks_stream stream,
+                                  perks_batch_stats *chosen);
+/* Fixes the plan parameters instead (granularity > 0, width_cap >= 0). */
+perks_status perks_batch_set_plan(perks_batch *b, double granularity, int32_t width_cap);
+
+/* ------------------------------------------------------------------------ */
 /* Conjugate gradient: Sec. 2.2.2 (algorithm), Sec. 4.3 (PERKS port)          */
 /* ------------------------------------------------------------------------ */
 
@@ -231,7 +279,17 @@ perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t nnz, const 
                               perks_op **out);
 perks_status perks_op_destroy(perks_op *op);
 
-/* y = A x for device vectors of n doubles (merge-path SpMV, one launch). */
+/* SpMV variant used inside CG and by perks_csr_spmv.  Both split the rows
+ * over blocks by the merge-path diagonal search (computed once).  Inside a
+ * block, ROWVEC gives each row to 8 lanes with direct coalesced loads and one
+ * fused multiply-add per nonzero (default); MERGE is the two-level merge-based
+ * SpMV of Sec. 4.3 (thread-level diagonal search over staged tiles, which
+ * also keeps A in shared memory when a block's slice fits).  Errors:
+ * INVALID_ARG. */
+enum { PERKS_SPMV_ROWVEC = 0, PERKS_SPMV_MERGE = 1 };
+perks_status perks_op_set_spmv(perks_op *op, int32_t kind);
+
+/* y = A x for device vectors of n doubles (one launch). */
 perks_status perks_csr_spmv(perks_op *op, const double *x, double *y, perks_stream stream);
 
 typedef struct {

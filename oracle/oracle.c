@@ -20,6 +20,11 @@
  *                        algorithm "Conjugate Gradient Solver"), with the stop
  *                        test read as <r,r> <= (rtol*||b||)^2 and a true-
  *                        residual recomputation on exit (restart if above).
+ *   oracle_stencil_run_lowp  The same update with fp32 or bf16 STORAGE (the
+ *                        library's low-precision modes): fp32 accumulation
+ *                        by fused multiply-add in table order, rounded to the
+ *                        storage type after every step.
+ *   oracle_bf16_round    float -> bf16 round-to-nearest-even (kept in a float).
  *   oracle_cg_fp32_ir    Textbook mixed-precision iterative refinement around
  *                        an fp32 CG (not in the paper; the library's FP32-IR
  *                        mode): fp64 residual and correction, fp32 inner CG.
@@ -108,6 +113,84 @@ int oracle_stencil_run(int ndim, int64_t nx, int64_t ny, int64_t nz, int radius,
                 out[(k * ny + j) * nx + i] =
                     a[((k + gz) * py + (j + gy)) * px + (i + gx)];
     free(a); free(b); free(delta);
+    return ORACLE_OK;
+}
+
+/* bf16 keeps the upper 16 bits of an IEEE binary32; rounding to nearest,
+ * ties to even, on the discarded 16 bits (finite inputs). */
+float oracle_bf16_round(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, sizeof(u));
+    uint32_t lsb = (u >> 16) & 1u;
+    u = u + 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    float y;
+    memcpy(&y, &u, sizeof(y));
+    return y;
+}
+
+/*
+ * Low-precision storage variant of oracle_stencil_run: `storage` 1 = fp32,
+ * 2 = bf16.  Cells (and the boundary and weights) are held as fp32 values of
+ * the storage type; each output is acc = fmaf(w[o], x(c+o), acc) over the
+ * table from acc = 0, then rounded to the storage type.  in/out are fp32
+ * arrays (bf16 values are exact in fp32).
+ */
+int oracle_stencil_run_lowp(int ndim, int64_t nx, int64_t ny, int64_t nz, int radius,
+                            int npts, const int32_t *off, const double *w,
+                            double boundary, int64_t steps, int storage,
+                            const float *in, float *out)
+{
+    if (ndim < 1 || ndim > 3 || nx < 1 || ny < 1 || nz < 1 || radius < 0 ||
+        npts < 1 || steps < 0 || (storage != 1 && storage != 2))
+        return ORACLE_ERR_ARG;
+    for (int o = 0; o < npts; ++o)
+        for (int d = 0; d < 3; ++d) {
+            int v = off[3 * o + d];
+            if (v < -radius || v > radius) return ORACLE_ERR_ARG;
+            if (d >= ndim && v != 0) return ORACLE_ERR_ARG;
+        }
+    const int64_t gx = (ndim >= 1) ? radius : 0;
+    const int64_t gy = (ndim >= 2) ? radius : 0;
+    const int64_t gz = (ndim >= 3) ? radius : 0;
+    const int64_t px = nx + 2 * gx, py = ny + 2 * gy, pz = nz + 2 * gz;
+    const int64_t total = px * py * pz;
+    float *a = (float *)malloc((size_t)total * sizeof(float));
+    float *b = (float *)malloc((size_t)total * sizeof(float));
+    int64_t *delta = (int64_t *)malloc((size_t)npts * sizeof(int64_t));
+    float *wf = (float *)malloc((size_t)npts * sizeof(float));
+    if (!a || !b || !delta || !wf) {
+        free(a); free(b); free(delta); free(wf);
+        return ORACLE_ERR_NOMEM;
+    }
+    float bnd = (float)boundary;
+    if (storage == 2) bnd = oracle_bf16_round(bnd);
+    for (int64_t i = 0; i < total; ++i) { a[i] = bnd; b[i] = bnd; }
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                a[((k + gz) * py + (j + gy)) * px + (i + gx)] = in[(k * ny + j) * nx + i];
+    for (int o = 0; o < npts; ++o) {
+        delta[o] = ((int64_t)off[3 * o + 2] * py + off[3 * o + 1]) * px + off[3 * o + 0];
+        wf[o] = (float)w[o];
+    }
+    for (int64_t s = 0; s < steps; ++s) {
+        for (int64_t k = 0; k < nz; ++k)
+            for (int64_t j = 0; j < ny; ++j)
+                for (int64_t i = 0; i < nx; ++i) {
+                    int64_t c = ((k + gz) * py + (j + gy)) * px + (i + gx);
+                    float acc = 0.0f;
+                    for (int o = 0; o < npts; ++o) acc = fmaf(wf[o], a[c + delta[o]], acc);
+                    b[c] = storage == 2 ? oracle_bf16_round(acc) : acc;
+                }
+        float *t = a; a = b; b = t;
+    }
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                out[(k * ny + j) * nx + i] = a[((k + gz) * py + (j + gy)) * px + (i + gx)];
+    free(a); free(b); free(delta); free(wf);
     return ORACLE_OK;
 }
 

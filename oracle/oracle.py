@@ -52,6 +52,11 @@ def _load():
         lib.oracle_stencil_run.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_int,
                                            ctypes.c_int, P, P, f64, i64, P, P]
         lib.oracle_stencil_run.restype = ctypes.c_int
+        lib.oracle_stencil_run_lowp.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_int,
+                                                ctypes.c_int, P, P, f64, i64, ctypes.c_int, P, P]
+        lib.oracle_stencil_run_lowp.restype = ctypes.c_int
+        lib.oracle_bf16_round.argtypes = [ctypes.c_float]
+        lib.oracle_bf16_round.restype = ctypes.c_float
         lib.oracle_csr_spmv.argtypes = [i32, P, P, P, P, P]
         lib.oracle_csr_spmv.restype = None
         lib.oracle_dot.argtypes = [i32, P, P]
@@ -92,6 +97,36 @@ def stencil_run(field: np.ndarray, offsets, weights, steps: int, boundary: float
     if st != OK:
         raise ValueError(f"oracle_stencil_run failed with status {st}")
     return out
+
+
+def stencil_run_lowp(field: np.ndarray, offsets, weights, steps: int, storage: str,
+                     boundary: float = 0.0, ndim: int | None = None,
+                     radius: int | None = None) -> np.ndarray:
+    """fp32 / bf16 storage variant (fp32 FMA accumulation, table order).
+
+    ``field`` holds values already of the storage type (as float32); returns
+    float32 values of the storage type."""
+    lib = _load()
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    nd = f.ndim if ndim is None else ndim
+    dims = list(f.shape[::-1]) + [1, 1, 1]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    r = int(np.abs(off).max()) if radius is None else radius
+    out = np.empty_like(f)
+    code = {"f32": 1, "bf16": 2}[storage]
+    st = lib.oracle_stencil_run_lowp(nd, dims[0], dims[1], dims[2], r, off.shape[0], _ptr(off),
+                                     _ptr(w), float(boundary), int(steps), code, _ptr(f), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_stencil_run_lowp failed with status {st}")
+    return out
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to bf16 (nearest, ties to even), returned as float32."""
+    lib = _load()
+    xs = np.asarray(x, dtype=np.float32).ravel()
+    return np.array([lib.oracle_bf16_round(float(v)) for v in xs], dtype=np.float32).reshape(np.shape(x))
 
 
 def _csr(rowptr, col, val):

@@ -19,6 +19,7 @@ MAX_POINTS = 125
 F64, F32, BF16 = 0, 1, 2
 PERSISTENT, PER_STEP = 0, 1
 CG_FP64, CG_FP32_IR, CG_FP64_MULTI = 0, 1, 2
+SPMV_ROWVEC, SPMV_MERGE = 0, 1
 
 STATUS = {
     0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "OUT_OF_MEMORY",
@@ -74,6 +75,18 @@ class CgStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("trace",)}
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("grid_blocks", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("max_tiles_per_block", ctypes.c_int32), ("width_cap", ctypes.c_int32),
+                ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
+                ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
+                ("granularity", ctypes.c_double), ("predicted_ms_per_step", ctypes.c_double),
+                ("algorithmic_bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _lock = threading.Lock()
 P = ctypes.c_void_p
@@ -103,6 +116,14 @@ def _declare(lib):
                             ctypes.POINTER(CgStats)], i32),
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
+        "perks_op_set_spmv": ([P, i32], i32),
+        "perks_batch_create": ([P, i32, ctypes.POINTER(StencilDesc), ctypes.POINTER(P)], i32),
+        "perks_batch_destroy": ([P], i32),
+        "perks_batch_set_field": ([P, i32, P, ctypes.c_int, P], i32),
+        "perks_batch_get_field": ([P, i32, P, ctypes.c_int, P], i32),
+        "perks_batch_run": ([P, i64, i32, P, ctypes.POINTER(BatchStats)], i32),
+        "perks_batch_autotune": ([P, i64, P, ctypes.POINTER(BatchStats)], i32),
+        "perks_batch_set_plan": ([P, f64, i32], i32),
     }
     for name, (args, res) in sigs.items():
         if not hasattr(lib, name):
@@ -272,11 +293,15 @@ class Stencil:
         self.dtype = dtype
         self.cells = int(np.prod(shape))
 
-    def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1):
+    def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1,
+                 scalar: bool = False):
+        """Plan override; ``scalar`` selects the one-cell-per-thread kernel
+        instead of the 16-byte-vector kernel."""
         p = StencilPlan()
         p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
         p.smem_cache_planes = int(smem_cache_planes)
         p.reg_cache = int(reg_cache)
+        p.reserved[0] = 1 if scalar else 0
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
 
     def reset_plan(self):
@@ -352,6 +377,10 @@ class CsrOperator:
         self.n = n
         self.nnz = nnz
 
+    def set_spmv(self, kind: int):
+        """SPMV_ROWVEC (default) or SPMV_MERGE (thread-level merge walk)."""
+        self.ctx.check(self._lib.perks_op_set_spmv(self.handle, int(kind)))
+
     def spmv(self, x, y, stream=None):
         xp, xd, _ = _buffer(x)
         yp, yd, _ = _buffer(y)
@@ -398,6 +427,62 @@ class CsrOperator:
     def close(self):
         if getattr(self, "handle", None):
             self._lib.perks_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many 2-D domains stepped together in one persistent launch (perks_batch_*).
+
+    ``domains`` is a sequence of dicts with ``shape`` (ny, nx), ``offsets`` and
+    ``weights`` (and optionally ``boundary``)."""
+
+    def __init__(self, ctx: Context, domains, dtype: str = "f32"):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        n = len(domains)
+        arr = (StencilDesc * n)()
+        for i, d in enumerate(domains):
+            arr[i] = _stencil_desc(d["shape"], d["offsets"], d["weights"], dtype,
+                                   d.get("boundary", 0.0), d.get("radius"))
+        h = P()
+        ctx.check(self._lib.perks_batch_create(ctx.handle, n, arr, ctypes.byref(h)))
+        self.handle = h
+        self.shapes = [tuple(d["shape"]) for d in domains]
+        self.dtype = dtype
+
+    def set_field(self, i: int, src, stream=None):
+        ptr, dev, _ = _buffer(src)
+        self.ctx.check(self._lib.perks_batch_set_field(self.handle, int(i), ptr, dev, _stream(stream)))
+
+    def get_field(self, i: int, dst, stream=None):
+        ptr, dev, _ = _buffer(dst)
+        self.ctx.check(self._lib.perks_batch_get_field(self.handle, int(i), ptr, dev, _stream(stream)))
+        return dst
+
+    def run(self, steps: int, variant: int = PERSISTENT, stream=None, stats: bool = False):
+        s = BatchStats() if stats else None
+        self.ctx.check(self._lib.perks_batch_run(self.handle, int(steps), int(variant), _stream(stream),
+                                                 ctypes.byref(s) if stats else None))
+        return s.as_dict() if stats else None
+
+    def autotune(self, probe_steps: int = 5, stream=None) -> dict:
+        s = BatchStats()
+        self.ctx.check(self._lib.perks_batch_autotune(self.handle, int(probe_steps), _stream(stream),
+                                                      ctypes.byref(s)))
+        return s.as_dict()
+
+    def set_plan(self, granularity: float = 1.0, width_cap: int = 0):
+        self.ctx.check(self._lib.perks_batch_set_plan(self.handle, float(granularity), int(width_cap)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_multi_spmv(const __grid_cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const CgSmem s = carve_cg_smem(smem_raw);
     const CgSlice sl = load_slice(a, s);
-    const double d = spmv_block<double>(a, s, sl, a.val, v, q, dotv);
+    const double d = spmv_any<double>(a, s, sl, a.val, v, q, dotv);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = d;
 }
 
@@ -208,6 +208,7 @@ struct perks_op {
     unsigned long long *bar = nullptr;
     DevError *err = nullptr;
     bool configured = false;
+    int spmv_kind = 0;
     int last_mode = 0;
     int last_status = 0;
     perks_status last_launch = 0;
@@ -255,6 +256,7 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.inner_rtol = inner_rtol;
     a.mode = mode;
     a.allow_cache = 1;
+    a.spmv_kind = op->spmv_kind;
     a.bar = op->bar;
     a.err = op->err;
     a.timeout_ns = op->ctx->timeout_ns;
@@ -544,4 +546,12 @@ extern "C" perks_status perks_cg_last_result(perks_op *op, perks_stream stream, 
     if (rc) return rc;
     perks_cg_stats local{};
     return read_result(op, (cudaStream_t)stream, stats ? stats : &local);
+}
+
+extern "C" perks_status perks_op_set_spmv(perks_op *op, int32_t kind) {
+    if (!op) return PERKS_ERR_INVALID_ARG;
+    if (kind != PERKS_SPMV_ROWVEC && kind != PERKS_SPMV_MERGE)
+        return fail(op->ctx, PERKS_ERR_INVALID_ARG, "op_set_spmv: unknown kind %d", kind);
+    op->spmv_kind = kind;
+    return PERKS_OK;
 }

@@ -13,9 +13,12 @@
 // in a fixed order (deterministic).
 //
 // Each tile's values, column indices and row ends are staged into shared
-// memory with cp.async, double-buffered so the next tile streams in while
-// the current one is computed; when a block's whole range fits, its tiles
-// stay in shared memory across iterations (the PERKS cache of A).
+// memory with cp.async, kCgBufs buffers deep so that kCgBufs-1 tiles stream
+// in while one is computed; when a block's whole range fits, its tiles stay
+// in shared memory across iterations (the PERKS cache of A).  The gathered
+// vector entries x[col] are staged next to them, so each nonzero costs one
+// fused multiply-add in the walk (GB300's fp64 pipe issues only 2 per clock
+// per SM, so the product is not formed separately).
 //
 // The CG recurrence, dot products and axpys are fused in the same
 // persistent loop with three grid barriers per iteration; grid-wide sums are
@@ -28,10 +31,10 @@
 namespace perks {
 
 constexpr int kCgThreads = 512;
-constexpr int kCgIpt = 8;
+constexpr int kCgIpt = 4;
 constexpr int kCgTile = kCgThreads * kCgIpt;  // merge-path items per tile
-constexpr int kCgMaxTiles = 1024;              // tiles per block
-constexpr int kCgBufs = 2;                     // tile buffers in shared memory
+constexpr int kCgMaxTiles = 2048;              // tiles per block
+constexpr int kCgBufs = 4;                     // tile buffers in shared memory (3 tiles in flight)
 
 enum CgMode : int { CGK_FP64 = 0, CGK_FP32_IR = 1, CGK_SPMV = 3 };
 
@@ -67,6 +70,7 @@ struct CgArgs {
     double inner_rtol;
     int mode;
     int allow_cache;
+    int spmv_kind;           // 0: row-vector SpMV (default), 1: thread-level merge walk
     const double *spmv_in;
     double *spmv_out;
     unsigned long long *bar;
@@ -260,32 +264,35 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
     double dot = 0.0;
     if (tid == 0) { s.tc_row[0] = -1; s.tc_val[0] = 0.0; }
     const bool cached = sl.cached;
-    if (!cached && sl.T > 0) stage_tile<V, true>(a, s, sl, 0, gval, tile_buf<V>(s, 0));
-    cp_async_commit();
-    for (int u = 0; u < sl.T; ++u) {
-        const TileBuf<V> tb = tile_buf<V>(s, cached ? u : (u & 1));
-        if (!cached) {
-            if (u + 1 < sl.T) stage_tile<V, true>(a, s, sl, u + 1, gval, tile_buf<V>(s, (u + 1) & 1));
+    if (!cached) {
+#pragma unroll
+        for (int k = 0; k < kCgBufs - 1; ++k) {
+            if (k < sl.T) stage_tile<V, true>(a, s, sl, k, gval, tile_buf<V>(s, k));
             cp_async_commit();
-            cp_async_wait<1>();
+        }
+    }
+    for (int u = 0; u < sl.T; ++u) {
+        const TileBuf<V> tb = tile_buf<V>(s, cached ? u : (u % kCgBufs));
+        if (!cached) {
+            const int un = u + kCgBufs - 1;
+            if (un < sl.T) stage_tile<V, true>(a, s, sl, un, gval, tile_buf<V>(s, un % kCgBufs));
+            cp_async_commit();
+            cp_async_wait<kCgBufs - 1>();
         }
         __syncthreads();  // (A) tile u staged; carry-in visible
         const int2 c0 = s.tiles[u], c1 = s.tiles[u + 1];
         const int nr = c1.x - c0.x, nzt = c1.y - c0.y;
         const int items = nr + nzt;
+        // gather the vector entries of the tile's nonzeros (coalesced over the tile)
+        V *xv = reinterpret_cast<V *>(s.prod);
+        for (int v = tid; v < nzt; v += blockDim.x) xv[v] = __ldcg(vin + tb.col[v]);
         const int d0 = min(tid * kCgIpt, items);
         const int d1 = min(d0 + kCgIpt, items);
         // thread-level merge search in shared memory: rows consumed at d0
         const long long jt = (long long)sl.jb + c0.y;  // global index of the tile's first nonzero
         const int x0 = merge_search(d0, nr, nzt, [&](int i) { return (long long)tb.re[i + 1] - jt; });
-        s.coord[tid] = make_int2(x0, d0 - x0);
-        if (tid == 0) s.coord[blockDim.x] = make_int2(nr, nzt);
-        __syncthreads();  // (B)
+        __syncthreads();  // (B) gathers visible
         const int y0 = d0 - x0;
-        const int y1 = s.coord[tid + 1].y;
-        // products of this thread's nonzeros (private slots of s.prod)
-        V *prod = reinterpret_cast<V *>(s.prod);
-        for (int v = y0; v < y1; ++v) prod[v] = tb.val[v] * __ldcg(vin + tb.col[v]);
         // walk the path: j is the global nonzero index, tb.re holds global row starts
         int i = x0;
         long long j = jt + y0;
@@ -295,7 +302,8 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
         V def_val = V(0);
         for (int it = d0; it < d1; ++it) {
             if (j < tb.re[i + 1]) {
-                acc += prod[j - jt];
+                const int v = (int)(j - jt);
+                acc = fma(tb.val[v], xv[v], acc);
                 ++j;
             } else {
                 const int row = sl.r0 + c0.x + i;
@@ -304,7 +312,7 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
                     def_val = acc;
                 } else {
                     vout[row] = acc;
-                    if (dotv) dot += (double)dotv[row] * (double)acc;
+                    if (dotv) dot = fma((double)dotv[row], (double)acc, dot);
                 }
                 acc = V(0);
                 ++i;
@@ -340,6 +348,73 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
     return block_sum(dot, s.red);
 }
 
+// Row-vector SpMV over the block's merge-path row range: sub-warps of kSub
+// lanes take kRowsPer consecutive rows each (a warp covers 32/kSub*kRowsPer
+// consecutive rows, so its loads are contiguous); the rows advance in
+// lockstep so their loads are independent and in flight together; each lane
+// strides over a row's nonzeros with direct coalesced loads and one fused
+// multiply-add per nonzero; the sub-warp sums by shuffles.  On GB300 this
+// costs ~8 instructions per nonzero against ~20 for the thread-level merge
+// walk; the block-level merge-path partition still balances the blocks.
+constexpr int kSub = 4;
+constexpr int kRowsPer = 4;
+
+template <typename V>
+__device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__restrict__ gval,
+                                 const V *__restrict__ vin, V *__restrict__ vout, const V *dotv, double *red) {
+    const int lane = threadIdx.x & (kSub - 1);
+    const int sub = threadIdx.x / kSub;
+    const int nsub = blockDim.x / kSub;
+    const unsigned mask = 0xffffffffu;
+    double dot = 0.0;
+    const int stride = nsub * kRowsPer;
+    for (int base = sl.r0; base < sl.r1; base += stride) {
+        const int row0 = base + sub * kRowsPer;
+        int jb[kRowsPer], je[kRowsPer];
+        V acc[kRowsPer];
+        int longest = 0;
+#pragma unroll
+        for (int k = 0; k < kRowsPer; ++k) {
+            const int r = row0 + k;
+            jb[k] = r < sl.r1 ? __ldg(a.rowptr + r) + lane : 0;
+            je[k] = r < sl.r1 ? __ldg(a.rowptr + r + 1) : 0;
+            acc[k] = V(0);
+            longest = max(longest, je[k] - jb[k] + lane);
+        }
+        for (int u = 0; u < longest; u += kSub) {
+#pragma unroll
+            for (int k = 0; k < kRowsPer; ++k) {
+                const int j = jb[k] + u;
+                if (j < je[k]) acc[k] = fma(__ldcs(gval + j), __ldcg(vin + __ldcs(a.col + j)), acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsPer; ++k) {
+#pragma unroll
+            for (int o = kSub / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(mask, acc[k], o, kSub);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kRowsPer; ++k) {
+                const int r = row0 + k;
+                if (r < sl.r1) {
+                    vout[r] = acc[k];
+                    if (dotv) dot = fma((double)dotv[r], (double)acc[k], dot);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return block_sum(dot, red);
+}
+
+template <typename V>
+__device__ __forceinline__ double spmv_any(const CgArgs &a, const CgSmem &s, const CgSlice &sl, const V *gval,
+                                           const V *vin, V *vout, const V *dotv) {
+    if (a.spmv_kind == 0 && !sl.cached) return spmv_block_vec<V>(a, sl, gval, vin, vout, dotv, s.red);
+    return spmv_block<V>(a, s, sl, gval, vin, vout, dotv);
+}
+
 __device__ __forceinline__ bool cg_sync(const CgArgs &a, unsigned long long &epoch) {
     return grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns);
 }
@@ -366,7 +441,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
     }
 
     if (a.mode == CGK_SPMV) {
-        spmv_block<double>(a, s, sl, a.val, a.spmv_in, a.spmv_out, nullptr);
+        spmv_any<double>(a, s, sl, a.val, a.spmv_in, a.spmv_out, nullptr);
         return;
     }
 
@@ -375,7 +450,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
     double *x = a.x, *r = a.r, *p = a.p, *q = a.q;
 
     // ---- r0 = b - A x0, ||b||^2
-    spmv_block<double>(a, s, sl, a.val, x, q, nullptr);
+    spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
     double bb_p = 0.0, rr_p = 0.0;
     for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
         const double ri = b[i] - q[i];
@@ -402,7 +477,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
             bool converged = false;
             while (it < a.max_iter) {
                 // A: q = A p, <p, q>
-                const double pq_p = spmv_block<double>(a, s, sl, a.val, p, q, p);
+                const double pq_p = spmv_any<double>(a, s, sl, a.val, p, q, p);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 // B: alpha; x += alpha p; r -= alpha q; <r, r>
@@ -435,7 +510,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             // C5: true residual in fp64
-            spmv_block<double>(a, s, sl, a.val, x, q, nullptr);
+            spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
             double tr_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
                 const double ri = b[i] - q[i];
@@ -473,7 +548,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
             const double itol2 = a.inner_rtol * a.inner_rtol * irr;
             if (!cg_sync(a, epoch)) return;
             while (it < a.max_iter) {
-                const double pq_p = spmv_block<float>(a, s, sl, a.val32, p32, q32, p32);
+                const double pq_p = spmv_any<float>(a, s, sl, a.val32, p32, q32, p32);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 const double pq = grid_sum(part0, G, s.red);
@@ -502,7 +577,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) x[i] += (double)d32[i];
             ++outer;
             if (!cg_sync(a, epoch)) return;
-            spmv_block<double>(a, s, sl, a.val, x, q, nullptr);
+            spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
             double tr_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
                 const double ri = b[i] - q[i];

@@ -34,14 +34,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// cp.async of one 4- or 8-byte element, cached in L1 (.ca is the only
-// variant for sizes below 16 bytes).
+// cp.async of one 4-, 8- or 16-byte element: 16-byte copies bypass L1
+// (.cg); smaller ones can only use .ca.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
     static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem_dst)),
-                 "l"(gmem_src), "n"(BYTES)
-                 : "memory");
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)),
+                     "l"(gmem_src)
+                     : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem_dst)),
+                     "l"(gmem_src), "n"(BYTES)
+                     : "memory");
+    }
 }
 
 __device__ __forceinline__ void cp_async_commit() {

@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "internal.h"
-#include "stencil_kernels.cuh"
+#include "stencil_registry.h"
 
 using namespace perks;
 
@@ -27,15 +27,7 @@ template <class SH> ShapeInfo shape_info(const char *name) {
     return ShapeInfo{SH::NDIM, SH::R, SH::BOX, SH::NPTS, name};
 }
 
-using S2d5 = Shape<2, 1, false>;
-using S3d7 = Shape<3, 1, false>;
-using S2d9 = Shape<2, 1, true>;
-using S2d25 = Shape<2, 2, true>;
-using S2ds9 = Shape<2, 2, false>;
-using S3d27 = Shape<3, 1, true>;
-using S3d13 = Shape<3, 2, false>;
-
-constexpr int kNumShapes = 7;
+constexpr int kNumShapes = SH_COUNT;
 
 const ShapeInfo &shape_by_id(int id) {
     static const ShapeInfo table[kNumShapes] = {
@@ -59,53 +51,66 @@ int shape_uoff(int id, int i, int axis) {
 
 // ------------------------------------------------------- kernel registry
 
-using PersistentFn = void (*)(PersistentArgs);
-
-struct KernelEntry {
-    PersistentFn fn = nullptr;
-    int nt = 0, zr = 0, d = 0;
-    bool configured = false;
-    int smem_budget = 0;  // dynamic shared memory available per block
-};
-
 constexpr int kPrefetch = 4;
 
 template <typename T, class SH, int NT, int ZR>
-KernelEntry entry() {
+KernelEntry entry(int dtype, int shape) {
     KernelEntry e;
+    e.dtype = dtype;
+    e.shape = shape;
+    e.per_step = false;
     e.fn = perks_stencil_kernel<T, SH, NT, ZR, kPrefetch>;
     e.nt = NT;
     e.zr = ZR;
     e.d = kPrefetch;
+    e.v = 1;
     return e;
 }
 
-// [dtype 0=f64,1=f32][shape][reg 0/1]
-KernelEntry &registry(int dtype, int shape, int reg) {
-    static KernelEntry table[2][kNumShapes][2];
+std::vector<KernelEntry> &registry() {
+    static std::vector<KernelEntry> table;
     static bool init = false;
     if (!init) {
         init = true;
-        table[0][0][0] = entry<double, S2d5, 256, 0>();
-        table[0][0][1] = entry<double, S2d5, 256, 16>();
-        table[1][0][0] = entry<float, S2d5, 256, 0>();
-        table[1][0][1] = entry<float, S2d5, 256, 16>();
-        table[0][1][0] = entry<double, S3d7, 1024, 0>();
-        table[0][1][1] = entry<double, S3d7, 1024, 8>();
-        table[1][1][0] = entry<float, S3d7, 1024, 0>();
-        table[1][1][1] = entry<float, S3d7, 1024, 8>();
-        table[0][2][0] = entry<double, S2d9, 256, 0>();
-        table[1][2][0] = entry<float, S2d9, 256, 0>();
-        table[0][3][0] = entry<double, S2d25, 256, 0>();
-        table[1][3][0] = entry<float, S2d25, 256, 0>();
-        table[0][4][0] = entry<double, S2ds9, 256, 0>();
-        table[1][4][0] = entry<float, S2ds9, 256, 0>();
-        table[0][5][0] = entry<double, S3d27, 1024, 0>();
-        table[1][5][0] = entry<float, S3d27, 1024, 0>();
-        table[0][6][0] = entry<double, S3d13, 1024, 0>();
-        table[1][6][0] = entry<float, S3d13, 1024, 0>();
+        // scalar kernels: any x extent (fp64 / fp32)
+        table.push_back(entry<double, S2d5, 256, 0>(PERKS_F64, SH_2D5));
+        table.push_back(entry<double, S2d5, 256, 16>(PERKS_F64, SH_2D5));
+        table.push_back(entry<float, S2d5, 256, 0>(PERKS_F32, SH_2D5));
+        table.push_back(entry<float, S2d5, 256, 16>(PERKS_F32, SH_2D5));
+        table.push_back(entry<double, S3d7, 1024, 0>(PERKS_F64, SH_3D7));
+        table.push_back(entry<float, S3d7, 1024, 0>(PERKS_F32, SH_3D7));
+        table.push_back(entry<double, S2d9, 256, 0>(PERKS_F64, SH_2D9));
+        table.push_back(entry<float, S2d9, 256, 0>(PERKS_F32, SH_2D9));
+        table.push_back(entry<double, S2d25, 256, 0>(PERKS_F64, SH_2D25));
+        table.push_back(entry<float, S2d25, 256, 0>(PERKS_F32, SH_2D25));
+        table.push_back(entry<double, S2ds9, 256, 0>(PERKS_F64, SH_2DS9));
+        table.push_back(entry<float, S2ds9, 256, 0>(PERKS_F32, SH_2DS9));
+        table.push_back(entry<double, S3d27, 1024, 0>(PERKS_F64, SH_3D27));
+        table.push_back(entry<float, S3d27, 1024, 0>(PERKS_F32, SH_3D27));
+        table.push_back(entry<double, S3d13, 1024, 0>(PERKS_F64, SH_3D13));
+        table.push_back(entry<float, S3d13, 1024, 0>(PERKS_F32, SH_3D13));
+        // vectorised kernels: x extent a multiple of V (16-byte vectors)
+        register_vec_f64(table);
+        register_vec_f32(table);
+        register_vec_bf16(table);
     }
-    return table[dtype][shape][reg];
+    return table;
+}
+
+// Picks a kernel: the vectorised one when the x extent allows 16-byte
+// vectors (unless the plan asks for the scalar kernel), the scalar one
+// otherwise; with or without the register cache as requested.
+KernelEntry *find_kernel(int dtype, int shape, bool want_reg, bool per_step, int X, bool allow_vec) {
+    KernelEntry *best = nullptr;
+    for (KernelEntry &e : registry()) {
+        if (e.dtype != dtype || e.shape != shape || e.per_step != per_step) continue;
+        if (e.v > 1 && (!allow_vec || X % e.v != 0)) continue;
+        auto score = [&](const KernelEntry &k) {
+            return (k.v > 1 ? 4 : 0) + ((k.zr > 0) == want_reg ? 2 : 0);
+        };
+        if (!best || score(e) > score(*best)) best = &e;
+    }
+    return best;
 }
 
 struct Plan {
@@ -169,20 +174,24 @@ int match_shape(const perks_stencil_desc &d, double *kw) {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-perks_status make_plan(perks_stencil *st, Plan &pl) {
+perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     perks_context *ctx = st->ctx;
     if (st->shape_id < 0)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "persistent kernel: offsets do not match a compiled shape "
                     "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt)");
-    if (st->desc.dtype == PERKS_BF16)
-        return fail(ctx, PERKS_ERR_UNSUPPORTED, "persistent kernel: BF16 storage is not built yet");
     const ShapeInfo &sh = shape_by_id(st->shape_id);
-    const int dt = st->desc.dtype == PERKS_F64 ? 0 : 1;
-    int reg = 1;
-    if (st->has_plan) reg = st->plan.reg_cache ? 1 : 0;
-    if (!registry(dt, st->shape_id, reg).fn) reg = 0;
-    KernelEntry &k = registry(dt, st->shape_id, reg);
+    bool want_reg = true, allow_vec = true;
+    if (st->has_plan) {
+        want_reg = st->plan.reg_cache != 0;
+        allow_vec = st->plan.reserved[0] == 0;  // reserved[0] = 1 forces the scalar kernel
+    }
+    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec);
+    if (!kp)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                    "no %s kernel for this dtype/shape/extent (bf16 needs nx divisible by 8)",
+                    per_step ? "per-step" : "persistent");
+    KernelEntry &k = *kp;
     if (!k.configured) {
         cudaFuncAttributes fa;
         PERKS_CUDA(ctx, cudaFuncGetAttributes(&fa, (const void *)k.fn));
@@ -196,6 +205,8 @@ perks_status make_plan(perks_stencil *st, Plan &pl) {
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
     const int S = 2 * RZ + 1 + k.d;
     const int es = st->es;
+    const int V = k.v;
+    const int HX = V > 1 ? std::max(V, 2) : RX;  // ring pad columns on each side
     int per_sm = 0;
     PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, k.nt,
                                                                   k.smem_budget));
@@ -204,23 +215,25 @@ perks_status make_plan(perks_stencil *st, Plan &pl) {
     const int maxG = per_sm * ctx->sm_count;
 
     const int X = st->X, Y = st->Y, Z = st->Z;
+    const int XU = X / V;  // x extent in units of V cells
     double best = 1e300;
     Plan bp;
     const int fx_lo = st->has_plan && st->plan.tiles_x > 0 ? st->plan.tiles_x : 1;
-    const int fx_hi = st->has_plan && st->plan.tiles_x > 0 ? st->plan.tiles_x : std::min(X, 512);
+    const int fx_hi = st->has_plan && st->plan.tiles_x > 0 ? st->plan.tiles_x : std::min(XU, 512);
     const int fy_lo = st->has_plan && st->plan.tiles_y > 0 ? st->plan.tiles_y : 1;
     const int fy_hi = st->has_plan && st->plan.tiles_y > 0 ? st->plan.tiles_y : std::min(Y, 512);
     for (int ntx = fx_lo; ntx <= fx_hi; ++ntx) {
-        const int txmax = ceil_div(X, ntx), txmin = X / ntx;
-        if (txmin < std::max(RX, 1)) break;
-        if (txmax > k.nt) continue;
+        const int txmax = ceil_div(XU, ntx) * V, txmin = (XU / ntx) * V;
+        if (txmin < std::max(RX, 1) || (V > 1 && txmin < 2)) break;
+        if (txmax / V > k.nt) continue;
         for (int nty = fy_lo; nty <= fy_hi; ++nty) {
             const int tymax = ceil_div(Y, nty), tymin = Y / nty;
             if (tymin < std::max(RY, 1)) break;
-            if ((long long)txmax * tymax > k.nt) continue;
-            const int nring = 2 * RY * (txmax + (sh.box ? 2 * RX : 0)) + 2 * RX * tymax;
+            if ((long long)(txmax / V) * tymax > k.nt) continue;
+            const int nring = V > 1 ? 2 * RY * (txmax / V) + (sh.box ? 4 * RY : 0) + 2 * tymax
+                                    : 2 * RY * (txmax + (sh.box ? 2 * RX : 0)) + 2 * RX * tymax;
             if (nring > k.nt) continue;
-            const int PW = txmax + 2 * RX, PH = tymax + 2 * RY;
+            const int PW = txmax + 2 * HX, PH = tymax + 2 * RY;
             const long long ring_bytes = (long long)S * PW * PH * es;
             if (ring_bytes > k.smem_budget) continue;
             int ntz;
@@ -253,6 +266,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl) {
     long long zs = (k.smem_budget - ring_bytes) / ((long long)bp.ncol * es);
     zs = std::min<long long>(zs, std::max(0, bp.tzmax - k.zr));
     if (st->has_plan && st->plan.smem_cache_planes >= 0) zs = std::min<long long>(zs, st->plan.smem_cache_planes);
+    if (per_step) zs = 0;
     bp.zs = (int)std::max<long long>(0, zs);
     bp.smem = ring_bytes + (long long)bp.zs * bp.ncol * es;
 
@@ -261,10 +275,11 @@ perks_status make_plan(perks_stencil *st, Plan &pl) {
     for (int t = 0; t < bp.blocks; ++t) {
         const int ti = t % bp.ntx, tj = (t / bp.ntx) % bp.nty, tk = t / (bp.ntx * bp.nty);
         int x0, tx, y0, ty, z0, tz;
-        split_axis(X, bp.ntx, ti, x0, tx);
+        split_axis(XU, bp.ntx, ti, x0, tx);
+        tx *= V;
         split_axis(Y, bp.nty, tj, y0, ty);
         split_axis(Z, bp.ntz, tk, z0, tz);
-        const int zc = std::min(tz, k.zr + bp.zs);
+        const int zc = per_step ? 0 : std::min(tz, k.zr + bp.zs);
         cached += (long long)zc * tx * ty;
         const int nfx = (ti > 0) + (ti + 1 < bp.ntx);
         const int nfy = (tj > 0) + (tj + 1 < bp.nty);
@@ -310,7 +325,8 @@ void fill_stats(const perks_stencil *st, const Plan *pl, long long steps, int va
 perks_status ensure_persistent_buffers(perks_stencil *st, const Plan &pl) {
     perks_context *ctx = st->ctx;
     const int RX = shape_by_id(st->shape_id).radius;
-    const size_t need = (size_t)pl.blocks * 2 * RX * pl.tzmax * pl.tymax * st->es;
+    const int width = pl.k->v > 1 ? 2 : RX;  // vector kernels store x-edges as pairs of cells
+    const size_t need = (size_t)pl.blocks * 2 * width * pl.tzmax * pl.tymax * st->es;
     if (need > st->faces_bytes) {
         for (int i = 0; i < 2; ++i) {
             if (st->faces[i]) cudaFree(st->faces[i]);
@@ -339,6 +355,21 @@ perks_status read_dev_error(perks_stencil *st, cudaStream_t s) {
     return PERKS_OK;
 }
 
+void fill_args(const perks_stencil *st, const Plan &pl, long long steps, PersistentArgs &a) {
+    std::memset(&a, 0, sizeof(a));
+    a.X = st->X; a.Y = st->Y; a.Z = st->Z;
+    a.XY = (long long)st->X * st->Y;
+    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
+    a.txmax = pl.txmax; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
+    a.PW = pl.PW; a.plane = pl.plane; a.ncol = pl.ncol;
+    a.zs = pl.zs;
+    a.steps = steps;
+    a.boundary = st->desc.boundary;
+    a.boundary_f = (float)st->desc.boundary;
+    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
+    a.face_plane = (long long)pl.tzmax * pl.tymax;
+}
+
 perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, Plan &pl) {
     perks_context *ctx = st->ctx;
     perks_status rc = make_plan(st, pl);
@@ -352,22 +383,11 @@ perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, 
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "persistent grid of %d blocks is not co-resident",
                     pl.blocks);
     PersistentArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.X = st->X; a.Y = st->Y; a.Z = st->Z;
-    a.XY = (long long)st->X * st->Y;
-    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
-    a.txmax = pl.txmax; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
-    a.PW = pl.PW; a.plane = pl.plane; a.ncol = pl.ncol;
-    a.zs = pl.zs;
-    a.steps = steps;
-    a.boundary = st->desc.boundary;
-    a.boundary_f = (float)st->desc.boundary;
-    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
+    fill_args(st, pl, steps, a);
     a.field[0] = st->field[st->cur];
     a.field[1] = st->field[st->cur ^ 1];
     a.faces[0] = st->faces[0];
     a.faces[1] = st->faces[1];
-    a.face_plane = (long long)pl.tzmax * pl.tymax;
     a.bar = st->bar;
     a.err = st->err;
     a.timeout_ns = ctx->timeout_ns;
@@ -377,6 +397,30 @@ perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, 
     PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)pl.k->fn, dim3(pl.blocks),
                                                 dim3(pl.k->nt), args, (size_t)pl.smem, s));
     if (steps & 1) st->cur ^= 1;
+    return PERKS_OK;
+}
+
+// One launch per step of the vectorised kernel body with no caches and no
+// grid barrier (the per-step baseline); false if no such kernel applies.
+perks_status run_per_step_vec(perks_stencil *st, long long steps, cudaStream_t s, bool &used) {
+    used = false;
+    if (st->shape_id < 0) return PERKS_OK;
+    if (!find_kernel(st->desc.dtype, st->shape_id, false, true, st->X, true)) return PERKS_OK;
+    perks_context *ctx = st->ctx;
+    Plan pl;
+    perks_status rc = make_plan(st, pl, true);
+    if (rc) return rc;
+    PersistentArgs a;
+    fill_args(st, pl, 1, a);
+    a.timeout_ns = ctx->timeout_ns;
+    for (long long k = 0; k < steps; ++k) {
+        a.field[0] = st->field[st->cur];
+        a.field[1] = st->field[st->cur ^ 1];
+        pl.k->fn<<<pl.blocks, pl.k->nt, (size_t)pl.smem, s>>>(a);
+        PERKS_CUDA(ctx, cudaGetLastError());
+        st->cur ^= 1;
+    }
+    used = true;
     return PERKS_OK;
 }
 
@@ -542,12 +586,14 @@ extern "C" perks_status perks_stencil_run(perks_stencil *st, int64_t steps, int3
         if (variant == PERKS_PERSISTENT) {
             rc = run_persistent(st, steps, s, pl);
             planned = true;
-        } else if (st->desc.dtype == PERKS_F64) {
-            rc = launch_steps<double>(st, steps, s);
-        } else if (st->desc.dtype == PERKS_F32) {
-            rc = launch_steps<float>(st, steps, s);
         } else {
-            rc = launch_steps<__nv_bfloat16>(st, steps, s);
+            bool used = false;
+            rc = run_per_step_vec(st, steps, s, used);
+            if (!rc && !used) {
+                if (st->desc.dtype == PERKS_F64) rc = launch_steps<double>(st, steps, s);
+                else if (st->desc.dtype == PERKS_F32) rc = launch_steps<float>(st, steps, s);
+                else rc = launch_steps<__nv_bfloat16>(st, steps, s);
+            }
         }
         if (rc) return rc;
     }
@@ -689,7 +735,8 @@ extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc
     perks_status rc = make_plan(&st, pl);
     if (rc) return rc;
     const int RX = shape_by_id(st.shape_id).radius;
-    const size_t face_bytes = (size_t)pl.blocks * 2 * RX * pl.tzmax * pl.tymax * es;
+    const int width = pl.k->v > 1 ? 2 : RX;
+    const size_t face_bytes = (size_t)pl.blocks * 2 * width * pl.tzmax * pl.tymax * es;
     if (2 * face_bytes > kNoallocFaceBytes) return PERKS_ERR_INVALID_ARG;  // edges exceed the scratch
 
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(scratch);
@@ -698,22 +745,11 @@ extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc
     unsigned char *faces = scratch + kNoallocHeaderBytes + kNoallocFieldBytes;
 
     PersistentArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.X = st.X; a.Y = st.Y; a.Z = st.Z;
-    a.XY = (long long)st.X * st.Y;
-    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
-    a.txmax = pl.txmax; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
-    a.PW = pl.PW; a.plane = pl.plane; a.ncol = pl.ncol;
-    a.zs = pl.zs;
-    a.steps = steps;
-    a.boundary = d.boundary;
-    a.boundary_f = (float)d.boundary;
-    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st.kw[i]; a.wf[i] = (float)st.kw[i]; }
+    fill_args(&st, pl, steps, a);
     a.field[0] = out;
     a.field[1] = field2;
     a.faces[0] = faces;
     a.faces[1] = faces + face_bytes;
-    a.face_plane = (long long)pl.tzmax * pl.tymax;
     a.bar = bar;
     a.err = err;
     a.timeout_ns = ctx.timeout_ns;

@@ -1,0 +1,39 @@
+// Registry of compiled persistent-stencil kernels, filled by the
+// translation units that instantiate them.
+#pragma once
+
+#include <vector>
+
+#include "stencil_kernels.cuh"
+
+namespace perks {
+
+using S2d5 = Shape<2, 1, false>;
+using S3d7 = Shape<3, 1, false>;
+using S2d9 = Shape<2, 1, true>;
+using S2d25 = Shape<2, 2, true>;
+using S2ds9 = Shape<2, 2, false>;
+using S3d27 = Shape<3, 1, true>;
+using S3d13 = Shape<3, 2, false>;
+
+// shape ids (the order of the table in stencil.cu)
+enum ShapeId : int { SH_2D5 = 0, SH_3D7, SH_2D9, SH_2D25, SH_2DS9, SH_3D27, SH_3D13, SH_COUNT };
+
+using PersistentFn = void (*)(PersistentArgs);
+
+struct KernelEntry {
+    int dtype = 0;          // PERKS_F64 / PERKS_F32 / PERKS_BF16
+    int shape = 0;          // ShapeId
+    bool per_step = false;  // one launch per step (no caches, no barrier)
+    PersistentFn fn = nullptr;
+    int nt = 0, zr = 0, d = 0;
+    int v = 1;              // cells per thread along x (1: scalar kernel)
+    bool configured = false;
+    int smem_budget = 0;    // dynamic shared memory available per block
+};
+
+void register_vec_f64(std::vector<KernelEntry> &out);
+void register_vec_f32(std::vector<KernelEntry> &out);
+void register_vec_bf16(std::vector<KernelEntry> &out);
+
+}  // namespace perks

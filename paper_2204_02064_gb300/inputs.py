@@ -162,3 +162,28 @@ SEED_3D = 1
 SEED_BATCH = 2
 SEED_CG = 3
 SEED_POISSON = 4
+
+
+# --------------------------------------------------------------------------
+# Batched uneven 2-D domains
+# --------------------------------------------------------------------------
+
+def batch_domains(count: int = 64, seed: int = SEED_BATCH, lo: int = 128, hi: int = 2048,
+                  multiple: int = 8):
+    """Square 2-D domains with sides log-uniform in [lo, hi], rounded to a
+    multiple of `multiple` cells (so rows split into 16-byte vectors for every
+    storage type); odd-indexed domains use the 3x3 box with weights 1/9,
+    even-indexed ones the 5x5 box with seeded positive weights summing to 1.
+    Returns a list of dicts (shape, name, offsets, weights, seed)."""
+    u = uniform(substream(seed, 11), count)
+    sides = np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+    sides = np.clip(np.round(sides / multiple) * multiple, lo, hi).astype(int)
+    out = []
+    for i, s in enumerate(sides):
+        if i % 2 == 1:
+            name, w = "2d9pt", workload_weights("2d9pt")
+        else:
+            name, w = "2d25pt", workload_weights("2d25pt", seed=substream(seed, 100 + i))
+        out.append(dict(shape=(int(s), int(s)), name=name, offsets=shape_offsets(name), weights=w,
+                        seed=substream(seed, 1000 + i)))
+    return out

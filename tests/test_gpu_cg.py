@@ -39,10 +39,11 @@ def _rows_abs(rp, c, v, x):
     return A @ np.abs(x)
 
 
-def _spmv_case(ctx, oracle, rp, c, v, seed):
+def _spmv_case(ctx, oracle, rp, c, v, seed, kind=0):
     n = len(rp) - 1
     x = inputs.cg_rhs(n, seed)
     op = _op(ctx, rp, c, v)
+    op.set_spmv(kind)
     y = torch.zeros(n, dtype=torch.float64, device="cuda")
     op.spmv(_dev(x), y)
     torch.cuda.synchronize()
@@ -51,13 +52,15 @@ def _spmv_case(ctx, oracle, rp, c, v, seed):
     assert np.max(np.abs(y.cpu().numpy() - ref) / scale) <= 1e-13
 
 
+@pytest.mark.parametrize("kind", [0, 1], ids=["rowvec", "merge"])
 @pytest.mark.parametrize("n,seed", [(7, 1), (2000, 2), (50000, 3), (300001, 4)])
-def test_spmv_synthetic(ctx, oracle, n, seed):
+def test_spmv_synthetic(ctx, oracle, n, seed, kind):
     rp, c, v = inputs.csr_spd_matrix(n, seed)
-    _spmv_case(ctx, oracle, rp, c, v, seed)
+    _spmv_case(ctx, oracle, rp, c, v, seed, kind)
 
 
-def test_spmv_long_rows_and_empty_rows(ctx, oracle):
+@pytest.mark.parametrize("kind", [0, 1], ids=["rowvec", "merge"])
+def test_spmv_long_rows_and_empty_rows(ctx, oracle, kind):
     """Rows longer than a tile (4096 path items) and empty rows exercise the
     thread- and tile-level carry fix-up."""
     rng = np.random.default_rng(5)
@@ -72,7 +75,7 @@ def test_spmv_long_rows_and_empty_rows(ctx, oracle):
     nnz = int(rp[-1])
     c = rng.integers(0, n, size=nnz).astype(np.int32)
     v = rng.standard_normal(nnz)
-    _spmv_case(ctx, oracle, rp.astype(np.int32), c, v, 6)
+    _spmv_case(ctx, oracle, rp.astype(np.int32), c, v, 6, kind)
 
 
 @pytest.fixture(scope="module")
@@ -82,9 +85,10 @@ def system_4k():
     return rp, c, v, inputs.cg_rhs(n, 31)
 
 
-def _solve(ctx, rp, c, v, b, mode, rtol=1e-10, x0=None, host=False, trace_len=0, **kw):
+def _solve(ctx, rp, c, v, b, mode, rtol=1e-10, x0=None, host=False, trace_len=0, spmv=0, **kw):
     from paper_2204_02064_gb300 import api
     op = _op(ctx, rp, c, v)
+    op.set_spmv(spmv)
     n = len(b)
     if host:
         x = np.zeros(n) if x0 is None else np.array(x0)
@@ -96,11 +100,12 @@ def _solve(ctx, rp, c, v, b, mode, rtol=1e-10, x0=None, host=False, trace_len=0,
     return x.cpu().numpy(), res
 
 
+@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
 @pytest.mark.parametrize("mode", [0, 2], ids=["persistent", "multi_launch"])
-def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode):
+def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode, spmv):
     rp, c, v, b = system_4k
     ref = oracle.cg(rp, c, v, b, rtol=1e-10, trace_len=20)
-    x, res = _solve(ctx, rp, c, v, b, mode, trace_len=20)
+    x, res = _solve(ctx, rp, c, v, b, mode, trace_len=20, spmv=spmv)
     tr = res["trace"]
     assert tr.shape == ref["trace"].shape
     assert np.max(np.abs(tr - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
@@ -109,12 +114,13 @@ def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode):
     assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
 
 
-def test_cg_fp32_ir(ctx, oracle, system_4k):
+@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
+def test_cg_fp32_ir(ctx, oracle, system_4k, spmv):
     from paper_2204_02064_gb300 import api
     rp, c, v, b = system_4k
     ref = oracle.cg(rp, c, v, b, rtol=1e-10)
     ir = oracle.cg_fp32_ir(rp, c, v, b, rtol=1e-10, inner_rtol=1e-4)
-    x, res = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, inner_rtol=1e-4)
+    x, res = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, inner_rtol=1e-4, spmv=spmv)
     assert res["true_rel_residual"] <= 1e-10
     assert res["outer_iterations"] >= 2
     assert abs(res["outer_iterations"] - ir["outer_iters"]) <= 1
@@ -130,14 +136,15 @@ def test_cg_host_buffers_and_initial_guess(ctx, oracle, system_4k):
     assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
 
 
-def test_cg_cached_and_streamed_agree(ctx, oracle):
-    # n=2000: every block's slice fits in shared memory (cached A);
-    # n=60000: three or more tiles per block, streamed each iteration.
+@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
+def test_cg_cached_and_streamed_agree(ctx, oracle, spmv):
+    # n=2000: every block's slice fits in shared memory (cached A, merge path);
+    # n=60000: several tiles per block, streamed each iteration.
     for n in (2000, 60000):
         rp, c, v = inputs.csr_spd_matrix(n, 8)
         b = inputs.cg_rhs(n, 8)
         ref = oracle.cg(rp, c, v, b, rtol=1e-10, trace_len=10)
-        x, res = _solve(ctx, rp, c, v, b, 0, trace_len=10)
+        x, res = _solve(ctx, rp, c, v, b, 0, trace_len=10, spmv=spmv)
         assert np.max(np.abs(res["trace"] - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
         assert res["true_rel_residual"] <= 1e-10
 

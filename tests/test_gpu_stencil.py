@@ -27,7 +27,7 @@ def rel_err(g, o):
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
 NP = {"f64": np.float64, "f32": np.float32}
-TT = {"f64": torch.float64, "f32": torch.float32}
+TT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
 
 
 @pytest.fixture(scope="module")
@@ -236,3 +236,59 @@ def test_full_size_sine_mode(ctx, L, steps, dtype):
     ref = (lam ** steps) * u
     err = ((out.double() - ref).abs().max() / ref.abs().max()).item()
     assert err <= (1e-11 if dtype == "f64" else 1e-4), (err, stats)
+
+
+# ------------------------------------------- fp32 / bf16 storage, bit-exact
+
+LOWP_CASES = [
+    ("3d7pt", (40, 36, 64), 15),
+    ("2d5pt", (130, 256), 40),
+    ("2d9pt", (97, 128), 12),
+    ("2d25pt", (97, 128), 9),
+    ("2ds9pt", (97, 128), 9),
+    ("3d27pt", (29, 33, 40), 5),
+    ("3d13pt", (29, 33, 40), 5),
+]
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["persistent", "per_step"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("name,shape,steps", LOWP_CASES)
+def test_lowp_storage_bit_exact(ctx, oracle, name, shape, steps, dtype, variant):
+    """fp32 / bf16 storage with fp32 FMA accumulation in table order: the GPU
+    and the low-precision oracle round identical values, so they agree bit for
+    bit; the error against the fp64 oracle is reported by the bench."""
+    from paper_2204_02064_gb300 import api
+    f = inputs.stencil_field(shape, 31).astype(np.float32)
+    src = torch.from_numpy(f).to(TT[dtype]).cuda()
+    f_store = src.float().cpu().numpy()
+    offs = inputs.shape_offsets(name)
+    w = inputs.workload_weights(name, seed=5)
+    ref = oracle.stencil_run_lowp(f_store, offs, w, steps, dtype)
+    st = api.Stencil(ctx, shape, offs, w, dtype=dtype)
+    st.set_field(src)
+    st.run(steps, variant=variant, stats=True)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    got = out.float().cpu().numpy()
+    assert np.array_equal(got, ref), float(np.max(np.abs(got - ref)))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_vector_and_scalar_kernels_agree(ctx, oracle, dtype):
+    f = inputs.stencil_field((36, 40, 64), 14)
+    a, sa = _run_gpu(ctx, "3d7pt", f, 17, dtype=dtype, plan=dict(tiles=(2, 3, 2)))
+    b, sb = _run_gpu(ctx, "3d7pt", f, 17, dtype=dtype, plan=dict(tiles=(2, 3, 2), scalar=True))
+    ref = _oracle(oracle, "3d7pt", f, 17)
+    assert rel_err(a, ref) <= TOL[dtype] and rel_err(b, ref) <= TOL[dtype]
+    if dtype == "f32":
+        assert np.array_equal(a, b)
+
+
+def test_bf16_needs_vector_width(ctx):
+    from paper_2204_02064_gb300 import api
+    st = api.Stencil(ctx, (20, 30), inputs.shape_offsets("2d5pt"), [0.2] * 5, dtype="bf16")
+    with pytest.raises(api.PerksError) as ei:
+        st.run(2, variant=0, stats=True)
+    assert ei.value.name == "UNSUPPORTED"

@@ -193,3 +193,40 @@ def test_zero_steps_is_identity(oracle):
 def test_rejects_offset_beyond_radius(oracle):
     with pytest.raises(ValueError):
         oracle.stencil_run(np.zeros((4, 4)), [(0, 0, 0), (2, 0, 0)], [0.5, 0.5], 1, radius=1)
+
+
+# --------------------------------------------- low-precision storage oracle
+
+def test_bf16_rounding_matches_torch(oracle):
+    torch = pytest.importorskip("torch")
+    x = (inputs.uniform(5, 4000) - 0.5) * np.float64(2.0) ** np.floor(inputs.uniform(6, 4000) * 40 - 20)
+    x = x.astype(np.float32)
+    # ties: values exactly halfway between two bf16 numbers
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8)], dtype=np.float32)
+    x = np.concatenate([x, ties])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle.bf16_round(x), ref)
+
+
+def test_lowp_fp32_close_to_fp64(oracle):
+    f = _field((17, 19, 23))
+    offs = inputs.shape_offsets("3d7pt")
+    w = inputs.workload_weights("3d7pt")
+    lo = oracle.stencil_run_lowp(f.astype(np.float32), offs, w, 30, "f32")
+    hi = oracle.stencil_run(f.astype(np.float32).astype(np.float64), offs, w, 30)
+    assert np.max(np.abs(lo - hi)) <= 30 * 8 * np.finfo(np.float32).eps
+
+
+def test_lowp_bf16_values_are_bf16_and_constant_preserved(oracle):
+    c = 0.75                                    # exact in bf16; weights 1/9 sum to 1
+    f = np.full((12, 13), c, dtype=np.float32)
+    out = oracle.stencil_run_lowp(f, inputs.shape_offsets("2d9pt"), inputs.workload_weights("2d9pt"),
+                                  20, "bf16", boundary=c)
+    assert np.array_equal(oracle.bf16_round(out), out)
+    assert np.max(np.abs(out - c)) <= 2.0 ** -8
+    g = oracle.bf16_round(_field((12, 13)).astype(np.float32))
+    o2 = oracle.stencil_run_lowp(g, inputs.shape_offsets("2d5pt"), [0.2] * 5, 7, "bf16")
+    assert np.array_equal(oracle.bf16_round(o2), o2)
+    # bf16 results track the fp64 oracle to a few bf16 ulps per step
+    ref = oracle.stencil_run(g.astype(np.float64), inputs.shape_offsets("2d5pt"), [0.2] * 5, 7)
+    assert np.max(np.abs(o2 - ref)) <= 7 * 2.0 ** -8
