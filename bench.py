@@ -153,6 +153,29 @@ def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1):
     return {"ms": times, "desc": desc, "cells": L ** 3}
 
 
+def stencil2d_leg(api, torch, ctx, L, steps, variant, K, W):
+    from paper_2204_02064_gb300 import inputs
+    f = torch.from_numpy(inputs.stencil_field((L, L), inputs.SEED_2D)).cuda()
+    st = api.Stencil(ctx, (L, L), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"))
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        st.set_field(f)
+        st.run(steps, variant)
+    times = []
+    for _ in range(K):
+        st.set_field(f)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.run(steps, variant)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st.check()
+    st.close()
+    return times
+
+
 def e2e_leg(api, torch, ctx, L, steps, K, W):
     """Host-buffer end-to-end: pinned H2D + persistent run + D2H, per step."""
     from paper_2204_02064_gb300 import inputs
@@ -336,12 +359,21 @@ def main():
     value = world * cells * args.steps / (total_ms * 1e-3) / 1e9
     mean_launch_ms = sum(per_run) / len(per_run)
     achieved = desc["algorithmic_bytes"] / (mean_launch_ms * 1e-3) / 1e9
+    # fp64 3d7pt: 7 fused multiply-adds per cell update = 14 FLOP
+    flop_per_cell = 2 * len(inputs.shape_offsets("3d7pt"))
+    tflops = cells * flop_per_cell / (mean_launch_ms * 1e-3) / 1e12
+    try:
+        sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        sm_mhz = 2070.0
+    fp64_peak = fp64_peak_tflops(info["sm_count"], sm_mhz)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
-            if tj.get("kernel_signature") == desc_signature(desc):
+            if (tj.get("kernel_signature") == desc_signature(desc)
+                    and tj.get("source_sha256") == _sources_sha(tj.get("source_files", []))):
                 traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             pass
@@ -355,6 +387,12 @@ def main():
             ps = stencil_leg(api, torch, ctx, L_3D, STEPS_3D, "f64", api.PER_STEP, 2, 1)
             variants["3d7pt_384_f64_per_step_baseline"] = {
                 "gcells": cells / (min(ps["ms"]) * 1e-3) / 1e9, "ms": min(ps["ms"])}
+            # the 2-D workload (2d5pt fp64 256^2, 100 steps): barrier-dominated
+            for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
+                r = stencil2d_leg(api, torch, ctx, 256, 100, var, 5, 2)
+                variants[f"2d5pt_256_f64_{vname}"] = {
+                    "gcells": 256 * 256 * 100 / (min(r) * 1e-3) / 1e9, "ms": min(r),
+                    "us_per_step": min(r) * 1e3 / 100}
             for L, dt in ((192, "f64"), (192, "f32"), (384, "f32")):
                 for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
                     r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, var, 2, 1)
@@ -395,12 +433,16 @@ def main():
                                                     "tiles_y", "tiles_z", "reg_cache_planes",
                                                     "smem_cache_planes", "cached_cells",
                                                     "halo_cells_per_step")}},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind,
-                         "kernel": "perks_stencil_kernel<double, 3d7pt>",
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp64_peak, "traffic": traffic,
+                         "peak_kind": "derived: 152 SMs x 2 fp64 FMA/clk x 2 FLOP x max SM clock "
+                                      f"{sm_mhz:.0f} MHz",
+                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, V=2, ZR=8, D=8>",
+                         "flop_per_cell_update": flop_per_cell,
                          "algorithmic_bytes_per_launch": desc["algorithmic_bytes"],
-                         "mean_launch_ms": mean_launch_ms},
+                         "mean_launch_ms": mean_launch_ms,
+                         "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak, "peak_kind": peak_kind}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -436,10 +478,11 @@ def profile_case(name):
             st.set_field(f)
             d = st.run(steps, stats=True)
             print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d}))
-    elif name.startswith("stencil3d"):
+    elif name.startswith("stencil3d") or name.startswith("stencil384"):
         dt = "f64" if "f64" in name else ("bf16" if "bf16" in name else "f32")
         variant = api.PER_STEP if name.endswith("perstep") else api.PERSISTENT
-        L, steps = 256, (4 if variant == api.PER_STEP else 20)
+        L = 384 if name.startswith("stencil384") else 256
+        steps = 4 if variant == api.PER_STEP else (8 if L == 384 else 20)
         shape = (L, L, L)
         f = torch.from_numpy(inputs.stencil_field(shape, 1)).to(
             {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]).cuda()
@@ -464,6 +507,21 @@ def profile_case(name):
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
     return 0
+
+
+def _sources_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def fp64_peak_tflops(sm_count, sm_mhz):
+    """GB300's FP64 pipe: 2 fused multiply-adds per clock per SM (1.25 TFLOP/s
+    nominal at 2.07 GHz on 152 SMs)."""
+    return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def desc_signature(desc):

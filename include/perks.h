@@ -322,6 +322,96 @@ perks_status perks_cg_solve(perks_op *op, const double *b, double *x, double rto
  * the last solve; returns that solve's status. */
 perks_status perks_cg_last_result(perks_op *op, perks_stream stream, perks_cg_stats *stats);
 
+/* ------------------------------------------------------------------------ */
+/* Batched variable-coefficient Poisson (learned warm start workload)         */
+/* ------------------------------------------------------------------------ */
+/* -div(k grad u) = f on nprob grids of nx*ny cells (5-point finite volumes,
+ * h = 1; face coefficient = harmonic mean of the two cells' k; Dirichlet 0
+ * through a ghost cell with the boundary cell's k), each solved by the CG of
+ * Sec. 2.2.2 in ONE persistent launch: each block owns a problem at a time
+ * and runs its whole CG loop with block-level reductions (the problems are
+ * independent, so no grid barrier is needed).  Not in the paper: this is the
+ * workload of the learned warm start. */
+typedef struct perks_poisson perks_poisson;
+
+typedef struct {
+    int32_t problems;
+    int32_t grid_blocks;
+    int32_t max_iterations;
+    double mean_iterations;
+    double max_true_rel_residual;     /* worst ||b - A x|| / ||b|| (fp64) */
+    int32_t *iterations;              /* optional host array, `capacity` entries */
+    double *true_rel_residual;        /* optional host array, `capacity` entries */
+    int32_t capacity;
+} perks_poisson_stats;
+
+/* k: nprob*ny*nx coefficients (x fastest, problem slowest), > 0; on_device
+ * says where k lives.  The library keeps the face coefficients and work
+ * vectors.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int32_t ny, int32_t nprob,
+                                  const double *k, int on_device, perks_poisson **out);
+perks_status perks_poisson_destroy(perks_poisson *p);
+/* y = A v for every problem; v, y: device arrays of nprob*nx*ny doubles. */
+perks_status perks_poisson_apply(perks_poisson *p, const double *v, double *y, perks_stream stream);
+/* Solves every problem to ||r|| <= rtol ||b|| from x (device arrays of
+ * nprob*nx*ny doubles; x holds x0 and receives the solutions).  With stats
+ * the stream is synchronized and the per-problem outcome reported; the call
+ * then returns the first failing problem's status. */
+perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, double rtol,
+                                 int32_t max_iter, perks_stream stream, perks_poisson_stats *stats);
+
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start for the Poisson workload                                */
+/* ------------------------------------------------------------------------ */
+/* A 4-layer convolutional network, u0 = scale * N(log k, f): 3x3 convolutions
+ * (2 -> 32 -> 32 -> 32 -> 1 channels, dilations d[0..3], zero padding), ReLU
+ * after the first three; activations stored in BF16 (or F32), products
+ * accumulated in fp32, fp32 master weights trained by Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on the mean squared error against u / scale.
+ * Parameter layout, per layer l: W_l[cout][cin][3][3] then b_l[cout].  Not
+ * in the paper: the warm start only chooses x0, CG still solves to the
+ * requested tolerance. */
+typedef struct perks_warmnet perks_warmnet;
+
+/* dilations: 4 values in 1..16 (NULL = {1, 2, 4, 8}); storage PERKS_BF16 or
+ * PERKS_F32; weights He-initialised from `seed`, biases 0.  Errors:
+ * INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+perks_status perks_warmnet_create(perks_context *ctx, const int32_t *dilations, int32_t storage,
+                                  uint64_t seed, perks_warmnet **out);
+perks_status perks_warmnet_destroy(perks_warmnet *net);
+int32_t perks_warmnet_num_params(const perks_warmnet *net);
+/* Copy the fp32 parameters to / from a host array of num_params floats. */
+perks_status perks_warmnet_get_params(perks_warmnet *net, float *host);
+perks_status perks_warmnet_set_params(perks_warmnet *net, const float *host);
+/* Output scale (> 0): the network predicts u / scale. */
+perks_status perks_warmnet_set_scale(perks_warmnet *net, float scale);
+float perks_warmnet_get_scale(const perks_warmnet *net);
+/* u = scale * N(log k, f) for nimg images of ny*nx cells; k, f, u are device
+ * arrays of nimg*ny*nx doubles (x fastest).  Asynchronous on `stream`. */
+perks_status perks_warmnet_predict(perks_warmnet *net, int32_t nimg, int32_t ny, int32_t nx,
+                                   const double *k, const double *f, double *u, perks_stream stream);
+/* Loss L = mean((N(log k, f) - u / scale)^2) and dL/dparams (host arrays;
+ * either may be NULL); synchronizes `stream`. */
+perks_status perks_warmnet_gradient(perks_warmnet *net, int32_t nimg, int32_t ny, int32_t nx,
+                                    const double *k, const double *f, const double *u,
+                                    float *grad_host, float *loss_host, perks_stream stream);
+/* One Adam step with learning rate lr on the batch (k, f, u); the loss before
+ * the step goes to *loss_host when non-NULL (then the stream is synchronized). */
+perks_status perks_warmnet_train_step(perks_warmnet *net, int32_t nimg, int32_t ny, int32_t nx,
+                                      const double *k, const double *f, const double *u, float lr,
+                                      perks_stream stream, float *loss_host);
+/* Trains for `epochs` passes over nimg pairs (k, f) -> u (device arrays as
+ * in predict), in minibatches of `batch` consecutive images visited in an
+ * order shuffled per epoch from `seed`, one Adam step (rate lr) per
+ * minibatch.  auto_scale = 1 first sets scale = rms(u).  epoch_loss (host,
+ * `epochs` floats, may be NULL) receives each epoch's mean minibatch loss.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+perks_status perks_warmnet_fit(perks_warmnet *net, int32_t nimg, int32_t ny, int32_t nx,
+                               const double *k, const double *f, const double *u, int32_t batch,
+                               int32_t epochs, float lr, int32_t auto_scale, uint64_t seed,
+                               perks_stream stream, float *epoch_loss);
+
 #ifdef __cplusplus
 }
 #endif

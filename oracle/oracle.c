@@ -25,6 +25,15 @@
  *                        by fused multiply-add in table order, rounded to the
  *                        storage type after every step.
  *   oracle_bf16_round    float -> bf16 round-to-nearest-even (kept in a float).
+ *   oracle_poisson_csr   5-point finite-volume operator of -div(k grad u) on an
+ *                        nx*ny grid (h = 1), face coefficient = harmonic mean
+ *                        of the two cells' k, Dirichlet 0 through a ghost
+ *                        cell with the boundary cell's own k; as CSR.
+ *   oracle_conv2d        2-D cross-correlation with zero padding and dilation
+ *                        (the warm-start network's layer), fp64.
+ *   oracle_warmnet_forward  The 4-layer network: conv+ReLU x3, conv; fp64.
+ *   oracle_warmnet_grad  Mean squared error of the network and its gradient
+ *                        by reverse-mode chain rule; fp64.
  *   oracle_cg_fp32_ir    Textbook mixed-precision iterative refinement around
  *                        an fp32 CG (not in the paper; the library's FP32-IR
  *                        mode): fp64 residual and correction, fp32 inner CG.
@@ -191,6 +200,185 @@ int oracle_stencil_run_lowp(int ndim, int64_t nx, int64_t ny, int64_t nz, int ra
             for (int64_t i = 0; i < nx; ++i)
                 out[(k * ny + j) * nx + i] = a[((k + gz) * py + (j + gy)) * px + (i + gx)];
     free(a); free(b); free(delta); free(wf);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Variable-coefficient Poisson operator and the warm-start network           */
+/* ------------------------------------------------------------------------ */
+
+static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+/* Writes the CSR matrix (rowptr: nx*ny+1, col/val: up to 5*nx*ny) of
+ * (Au)_c = sum over the 4 faces of c of kf * (u_c - u_nb), u_nb = 0 outside;
+ * kf = harmonic mean of k_c and k_nb inside, k_c on the boundary.  Cell (i,j)
+ * is row j*nx + i; columns ascend within a row.  Returns nnz. */
+int64_t oracle_poisson_csr(int32_t nx, int32_t ny, const double *k, int32_t *rowptr,
+                           int32_t *col, double *val)
+{
+    int64_t nz = 0;
+    rowptr[0] = 0;
+    for (int32_t j = 0; j < ny; ++j)
+        for (int32_t i = 0; i < nx; ++i) {
+            const int32_t c = j * nx + i;
+            const double kc = k[c];
+            const double fs = j > 0 ? harmonic(kc, k[c - nx]) : kc;
+            const double fw = i > 0 ? harmonic(kc, k[c - 1]) : kc;
+            const double fe = i + 1 < nx ? harmonic(kc, k[c + 1]) : kc;
+            const double fn = j + 1 < ny ? harmonic(kc, k[c + nx]) : kc;
+            if (j > 0) { col[nz] = c - nx; val[nz] = -fs; ++nz; }
+            if (i > 0) { col[nz] = c - 1; val[nz] = -fw; ++nz; }
+            double d = fs + fw;
+            d = d + fe;
+            d = d + fn;
+            col[nz] = c; val[nz] = d; ++nz;
+            if (i + 1 < nx) { col[nz] = c + 1; val[nz] = -fe; ++nz; }
+            if (j + 1 < ny) { col[nz] = c + nx; val[nz] = -fn; ++nz; }
+            rowptr[c + 1] = (int32_t)nz;
+        }
+    return nz;
+}
+
+/* out[co][y][x] = b[co] + sum_ci sum_ky sum_kx w[co][ci][ky][kx] *
+ *                 in[ci][y + (ky-1)*dil][x + (kx-1)*dil], zero outside. */
+void oracle_conv2d(int32_t cin, int32_t cout, int32_t h, int32_t w, int32_t dil,
+                   const double *in, const double *wt, const double *bias, double *out)
+{
+    for (int32_t co = 0; co < cout; ++co)
+        for (int32_t y = 0; y < h; ++y)
+            for (int32_t x = 0; x < w; ++x) {
+                double acc = bias ? bias[co] : 0.0;
+                for (int32_t ci = 0; ci < cin; ++ci)
+                    for (int32_t ky = 0; ky < 3; ++ky)
+                        for (int32_t kx = 0; kx < 3; ++kx) {
+                            const int32_t yy = y + (ky - 1) * dil, xx = x + (kx - 1) * dil;
+                            if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                            double t = wt[((co * cin + ci) * 3 + ky) * 3 + kx] *
+                                       in[((int64_t)ci * h + yy) * w + xx];
+                            acc = acc + t;
+                        }
+                out[((int64_t)co * h + y) * w + x] = acc;
+            }
+}
+
+/* Network: channels c0 -> c1 -> c1 -> c1 -> 1, dilations dil[0..3], ReLU
+ * after the first three layers.  params holds, per layer, the weights
+ * [cout][cin][3][3] followed by the biases [cout].  out: h*w. */
+int oracle_warmnet_forward(int32_t c0, int32_t c1, int32_t h, int32_t w, const int32_t *dil,
+                           const double *params, const double *in, double *out)
+{
+    const int32_t cins[4] = {c0, c1, c1, c1}, couts[4] = {c1, c1, c1, 1};
+    double *a = (double *)malloc((size_t)c1 * h * w * sizeof(double));
+    double *b = (double *)malloc((size_t)c1 * h * w * sizeof(double));
+    if (!a || !b) { free(a); free(b); return ORACLE_ERR_NOMEM; }
+    const double *x = in;
+    const double *p = params;
+    for (int l = 0; l < 4; ++l) {
+        double *y = (l == 3) ? out : ((l % 2 == 0) ? a : b);
+        const double *wt = p;
+        const double *bias = p + (int64_t)couts[l] * cins[l] * 9;
+        oracle_conv2d(cins[l], couts[l], h, w, dil[l], x, wt, bias, y);
+        if (l < 3)
+            for (int64_t i = 0; i < (int64_t)couts[l] * h * w; ++i) y[i] = y[i] > 0.0 ? y[i] : 0.0;
+        p = bias + couts[l];
+        x = y;
+    }
+    free(a); free(b);
+    return ORACLE_OK;
+}
+
+/* Mean squared error of the network over nimg images and its gradient with
+ * respect to every parameter, by the chain rule written out layer by layer
+ * (reverse-mode differentiation of the forward pass above):
+ *   L = (1/N) sum (out - t)^2,  N = nimg*h*w,   dL/dout = 2 (out - t) / N;
+ *   for a layer y = conv(x; W, b):  dL/db[co] = sum_p dy[co][p],
+ *     dL/dW[co][ci][ky][kx] = sum_p dy[co][p] * x[ci][p + off(ky,kx)],
+ *     dL/dx[ci][q] = sum_co sum_(ky,kx) W[co][ci][ky][kx] * dy[co][q - off(ky,kx)];
+ *   through a ReLU: dL/dz = dL/dy where y = max(z, 0) > 0, else 0.
+ * in: nimg*c0*h*w, t: nimg*h*w, grad: same layout as params (overwritten).
+ * Returns the loss through *loss. */
+int oracle_warmnet_grad(int32_t nimg, int32_t c0, int32_t c1, int32_t h, int32_t w, const int32_t *dil,
+                        const double *params, const double *in, const double *t, double *loss, double *grad)
+{
+    const int32_t cins[4] = {c0, c1, c1, c1}, couts[4] = {c1, c1, c1, 1};
+    const int64_t hw = (int64_t)h * w, N = (int64_t)nimg * hw;
+    int64_t woff[4], boff[4], np = 0;
+    for (int l = 0; l < 4; ++l) {
+        woff[l] = np; np += (int64_t)couts[l] * cins[l] * 9;
+        boff[l] = np; np += couts[l];
+    }
+    for (int64_t i = 0; i < np; ++i) grad[i] = 0.0;
+    double *act[5];          /* act[0] = input, act[l+1] = output of layer l (after ReLU) */
+    double *dy = (double *)malloc((size_t)c1 * hw * sizeof(double));
+    double *dx = (double *)malloc((size_t)c1 * hw * sizeof(double));
+    int ok = dy && dx;
+    for (int l = 1; l <= 4; ++l) {
+        act[l] = (double *)malloc((size_t)couts[l - 1] * hw * sizeof(double));
+        ok = ok && act[l];
+    }
+    if (!ok) {
+        free(dy); free(dx);
+        for (int l = 1; l <= 4; ++l) free(act[l]);
+        return ORACLE_ERR_NOMEM;
+    }
+    double L = 0.0;
+    for (int32_t img = 0; img < nimg; ++img) {
+        act[0] = (double *)(in + (int64_t)img * c0 * hw);
+        for (int l = 0; l < 4; ++l) {
+            oracle_conv2d(cins[l], couts[l], h, w, dil[l], act[l], params + woff[l], params + boff[l], act[l + 1]);
+            if (l < 3)
+                for (int64_t i = 0; i < (int64_t)couts[l] * hw; ++i)
+                    act[l + 1][i] = act[l + 1][i] > 0.0 ? act[l + 1][i] : 0.0;
+        }
+        const double *ti = t + (int64_t)img * hw;
+        for (int64_t p = 0; p < hw; ++p) {
+            const double d = act[4][p] - ti[p];
+            L = L + d * d / (double)N;
+            dy[p] = 2.0 * d / (double)N;
+        }
+        for (int l = 3; l >= 0; --l) {
+            const int32_t ci_n = cins[l], co_n = couts[l], d = dil[l];
+            const double *x = act[l];
+            const double *W = params + woff[l];
+            double *gW = grad + woff[l], *gb = grad + boff[l];
+            for (int32_t co = 0; co < co_n; ++co)
+                for (int64_t p = 0; p < hw; ++p) gb[co] = gb[co] + dy[co * hw + p];
+            for (int32_t co = 0; co < co_n; ++co)
+                for (int32_t ci = 0; ci < ci_n; ++ci)
+                    for (int32_t ky = 0; ky < 3; ++ky)
+                        for (int32_t kx = 0; kx < 3; ++kx) {
+                            double acc = 0.0;
+                            for (int32_t y = 0; y < h; ++y)
+                                for (int32_t xq = 0; xq < w; ++xq) {
+                                    const int32_t yy = y + (ky - 1) * d, xx = xq + (kx - 1) * d;
+                                    if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                                    acc = acc + dy[co * hw + (int64_t)y * w + xq] * x[ci * hw + (int64_t)yy * w + xx];
+                                }
+                            double *g = &gW[((co * ci_n + ci) * 3 + ky) * 3 + kx];
+                            *g = *g + acc;
+                        }
+            if (l == 0) break;
+            for (int64_t i = 0; i < (int64_t)ci_n * hw; ++i) dx[i] = 0.0;
+            for (int32_t co = 0; co < co_n; ++co)
+                for (int32_t ci = 0; ci < ci_n; ++ci)
+                    for (int32_t ky = 0; ky < 3; ++ky)
+                        for (int32_t kx = 0; kx < 3; ++kx) {
+                            const double wv = W[((co * ci_n + ci) * 3 + ky) * 3 + kx];
+                            for (int32_t y = 0; y < h; ++y)
+                                for (int32_t xq = 0; xq < w; ++xq) {
+                                    const int32_t yy = y + (ky - 1) * d, xx = xq + (kx - 1) * d;
+                                    if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                                    double *g = &dx[ci * hw + (int64_t)yy * w + xx];
+                                    *g = *g + wv * dy[co * hw + (int64_t)y * w + xq];
+                                }
+                        }
+            /* ReLU of layer l-1: its output is x = act[l] */
+            for (int64_t i = 0; i < (int64_t)ci_n * hw; ++i) dy[i] = x[i] > 0.0 ? dx[i] : 0.0;
+        }
+    }
+    *loss = L;
+    free(dy); free(dx);
+    for (int l = 1; l <= 4; ++l) free(act[l]);
     return ORACLE_OK;
 }
 

@@ -57,6 +57,14 @@ def _load():
         lib.oracle_stencil_run_lowp.restype = ctypes.c_int
         lib.oracle_bf16_round.argtypes = [ctypes.c_float]
         lib.oracle_bf16_round.restype = ctypes.c_float
+        lib.oracle_poisson_csr.argtypes = [i32, i32, P, P, P, P]
+        lib.oracle_poisson_csr.restype = i64
+        lib.oracle_conv2d.argtypes = [i32, i32, i32, i32, i32, P, P, P, P]
+        lib.oracle_conv2d.restype = None
+        lib.oracle_warmnet_forward.argtypes = [i32, i32, i32, i32, P, P, P, P]
+        lib.oracle_warmnet_forward.restype = ctypes.c_int
+        lib.oracle_warmnet_grad.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, P]
+        lib.oracle_warmnet_grad.restype = ctypes.c_int
         lib.oracle_csr_spmv.argtypes = [i32, P, P, P, P, P]
         lib.oracle_csr_spmv.restype = None
         lib.oracle_dot.argtypes = [i32, P, P]
@@ -186,3 +194,61 @@ def cg_fp32_ir(rowptr, col, val, b, x0=None, rtol: float = 1e-10, inner_rtol: fl
                                ctypes.byref(inner), ctypes.byref(outer), ctypes.byref(tr))
     return dict(x=x, status=st, inner_iters=inner.value, outer_iters=outer.value,
                 true_rel=tr.value)
+
+
+def poisson_csr(k: np.ndarray):
+    """CSR of the finite-volume operator for the coefficient field k (ny, nx)."""
+    lib = _load()
+    kk = np.ascontiguousarray(k, dtype=np.float64)
+    ny, nx = kk.shape
+    n = nx * ny
+    rp = np.empty(n + 1, dtype=np.int32)
+    c = np.empty(5 * n, dtype=np.int32)
+    v = np.empty(5 * n, dtype=np.float64)
+    nnz = lib.oracle_poisson_csr(nx, ny, _ptr(kk), _ptr(rp), _ptr(c), _ptr(v))
+    return rp, c[:nnz].copy(), v[:nnz].copy()
+
+
+def conv2d(x: np.ndarray, w: np.ndarray, b=None, dil: int = 1) -> np.ndarray:
+    """x: (cin, h, w); w: (cout, cin, 3, 3); returns (cout, h, w)."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    cin, h, wd = xx.shape
+    cout = ww.shape[0]
+    bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty((cout, h, wd))
+    lib.oracle_conv2d(cin, cout, h, wd, dil, _ptr(xx), _ptr(ww), _ptr(bb) if bb is not None else None,
+                      _ptr(out))
+    return out
+
+
+def warmnet_forward(params: np.ndarray, x: np.ndarray, c1: int, dil=(1, 2, 4, 8)) -> np.ndarray:
+    """Forward pass of the 4-layer warm-start network on one input (c0, h, w)."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    c0, h, w = xx.shape
+    pp = np.ascontiguousarray(params, dtype=np.float64)
+    dd = np.ascontiguousarray(dil, dtype=np.int32)
+    out = np.empty((h, w))
+    st = lib.oracle_warmnet_forward(c0, c1, h, w, _ptr(dd), _ptr(pp), _ptr(xx), _ptr(out))
+    if st != OK:
+        raise ValueError("oracle_warmnet_forward failed")
+    return out
+
+
+def warmnet_grad(params: np.ndarray, x: np.ndarray, t: np.ndarray, c1: int, dil=(1, 2, 4, 8)):
+    """Loss mean((N(x) - t)^2) over a batch x (nimg, c0, h, w) with targets
+    t (nimg, h, w), and its gradient (same layout as params)."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    nimg, c0, h, w = xx.shape
+    tt = np.ascontiguousarray(t, dtype=np.float64).reshape(nimg, h, w)
+    pp = np.ascontiguousarray(params, dtype=np.float64)
+    dd = np.ascontiguousarray(dil, dtype=np.int32)
+    g = np.empty_like(pp)
+    loss = np.zeros(1)
+    st = lib.oracle_warmnet_grad(nimg, c0, c1, h, w, _ptr(dd), _ptr(pp), _ptr(xx), _ptr(tt), _ptr(loss), _ptr(g))
+    if st != OK:
+        raise ValueError("oracle_warmnet_grad failed")
+    return float(loss[0]), g

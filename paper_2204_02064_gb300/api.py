@@ -87,6 +87,14 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PoissonStats(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+                ("max_iterations", ctypes.c_int32), ("mean_iterations", ctypes.c_double),
+                ("max_true_rel_residual", ctypes.c_double),
+                ("iterations", ctypes.POINTER(ctypes.c_int32)),
+                ("true_rel_residual", ctypes.POINTER(ctypes.c_double)), ("capacity", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 P = ctypes.c_void_p
@@ -117,6 +125,22 @@ def _declare(lib):
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_op_set_spmv": ([P, i32], i32),
+        "perks_poisson_create": ([P, i32, i32, i32, P, ctypes.c_int, ctypes.POINTER(P)], i32),
+        "perks_poisson_destroy": ([P], i32),
+        "perks_poisson_apply": ([P, P, P, P], i32),
+        "perks_poisson_solve": ([P, P, P, f64, i32, P, ctypes.POINTER(PoissonStats)], i32),
+        "perks_warmnet_create": ([P, P, i32, ctypes.c_uint64, ctypes.POINTER(P)], i32),
+        "perks_warmnet_destroy": ([P], i32),
+        "perks_warmnet_num_params": ([P], i32),
+        "perks_warmnet_get_params": ([P, P], i32),
+        "perks_warmnet_set_params": ([P, P], i32),
+        "perks_warmnet_set_scale": ([P, ctypes.c_float], i32),
+        "perks_warmnet_get_scale": ([P], ctypes.c_float),
+        "perks_warmnet_predict": ([P, i32, i32, i32, P, P, P, P], i32),
+        "perks_warmnet_gradient": ([P, i32, i32, i32, P, P, P, P, P, P], i32),
+        "perks_warmnet_train_step": ([P, i32, i32, i32, P, P, P, ctypes.c_float, P, P], i32),
+        "perks_warmnet_fit": ([P, i32, i32, i32, P, P, P, i32, i32, ctypes.c_float, i32,
+                               ctypes.c_uint64, P, P], i32),
         "perks_batch_create": ([P, i32, ctypes.POINTER(StencilDesc), ctypes.POINTER(P)], i32),
         "perks_batch_destroy": ([P], i32),
         "perks_batch_set_field": ([P, i32, P, ctypes.c_int, P], i32),
@@ -490,3 +514,161 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Poisson:
+    """Batched variable-coefficient Poisson problems (perks_poisson_*).
+
+    ``k`` is an array/tensor of shape (nprob, ny, nx) of positive coefficients."""
+
+    def __init__(self, ctx: Context, k):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        shape = tuple(k.shape)
+        if len(shape) != 3:
+            raise ValueError("k must be (nprob, ny, nx)")
+        self.nprob, self.ny, self.nx = (int(v) for v in shape)
+        ptr, dev, nbytes = _buffer(k)
+        if nbytes != 8 * self.nprob * self.ny * self.nx:
+            raise ValueError("k must be float64")
+        h = P()
+        ctx.check(self._lib.perks_poisson_create(ctx.handle, self.nx, self.ny, self.nprob, ptr, dev,
+                                                 ctypes.byref(h)))
+        self.handle = h
+
+    def apply(self, v, y, stream=None):
+        vp, vd, _ = _buffer(v)
+        yp, yd, _ = _buffer(y)
+        if not (vd and yd):
+            raise ValueError("apply takes device tensors")
+        self.ctx.check(self._lib.perks_poisson_apply(self.handle, vp, yp, _stream(stream)))
+
+    def solve(self, b, x, rtol: float = 1e-8, max_iter: int = 20000, stream=None, stats: bool = True):
+        bp, bd, _ = _buffer(b)
+        xp, xd, _ = _buffer(x)
+        if not (bd and xd):
+            raise ValueError("solve takes device tensors")
+        if not stats:
+            self.ctx.check(self._lib.perks_poisson_solve(self.handle, bp, xp, float(rtol), int(max_iter),
+                                                         _stream(stream), None))
+            return None
+        it = np.zeros(self.nprob, dtype=np.int32)
+        tr = np.zeros(self.nprob, dtype=np.float64)
+        s = PoissonStats()
+        s.iterations = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        s.true_rel_residual = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        s.capacity = self.nprob
+        self.ctx.check(self._lib.perks_poisson_solve(self.handle, bp, xp, float(rtol), int(max_iter),
+                                                     _stream(stream), ctypes.byref(s)))
+        return {"iterations": it, "true_rel_residual": tr, "max_iterations": s.max_iterations,
+                "mean_iterations": s.mean_iterations, "grid_blocks": s.grid_blocks,
+                "max_true_rel_residual": s.max_true_rel_residual}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_poisson_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmNet:
+    """The learned warm start (perks_warmnet_*): a 4-layer 3x3 conv network
+    mapping (log k, f) to a first guess of u.  Images are device float64
+    tensors of shape (nimg, ny, nx)."""
+
+    def __init__(self, ctx: Context, storage: int = BF16, dilations=(1, 2, 4, 8), seed: int = 0):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        d = np.ascontiguousarray(dilations, dtype=np.int32)
+        h = P()
+        ctx.check(self._lib.perks_warmnet_create(ctx.handle, d.ctypes.data, int(storage), int(seed),
+                                                 ctypes.byref(h)))
+        self.handle = h
+        self.num_params = int(self._lib.perks_warmnet_num_params(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.perks_warmnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self.ctx.check(self._lib.perks_warmnet_get_params(self.handle, out.ctypes.data))
+        return out
+
+    @params.setter
+    def params(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        if v.size != self.num_params:
+            raise ValueError("expected %d parameters" % self.num_params)
+        self.ctx.check(self._lib.perks_warmnet_set_params(self.handle, v.ctypes.data))
+
+    @property
+    def scale(self) -> float:
+        return float(self._lib.perks_warmnet_get_scale(self.handle))
+
+    @scale.setter
+    def scale(self, value: float):
+        self.ctx.check(self._lib.perks_warmnet_set_scale(self.handle, float(value)))
+
+    @staticmethod
+    def _dims(t):
+        shape = tuple(t.shape)
+        if len(shape) != 3:
+            raise ValueError("images must be (nimg, ny, nx)")
+        return shape
+
+    def _ptrs(self, *ts):
+        out = []
+        for t in ts:
+            p, dev, nbytes = _buffer(t)
+            if not dev:
+                raise ValueError("warm-start network takes device tensors")
+            if nbytes != 8 * int(np.prod(tuple(t.shape))) or tuple(t.shape) != tuple(ts[0].shape):
+                raise ValueError("images must be float64 tensors of one shape")
+            out.append(p)
+        return out
+
+    def predict(self, k, f, u, stream=None):
+        nimg, ny, nx = self._dims(k)
+        kp, fp, up = self._ptrs(k, f, u)
+        self.ctx.check(self._lib.perks_warmnet_predict(self.handle, nimg, ny, nx, kp, fp, up, _stream(stream)))
+
+    def gradient(self, k, f, u, stream=None):
+        nimg, ny, nx = self._dims(k)
+        kp, fp, up = self._ptrs(k, f, u)
+        g = np.empty(self.num_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self.ctx.check(self._lib.perks_warmnet_gradient(self.handle, nimg, ny, nx, kp, fp, up, g.ctypes.data,
+                                                        loss.ctypes.data, _stream(stream)))
+        return float(loss[0]), g
+
+    def train_step(self, k, f, u, lr: float = 1e-3, stream=None) -> float:
+        nimg, ny, nx = self._dims(k)
+        kp, fp, up = self._ptrs(k, f, u)
+        loss = np.zeros(1, dtype=np.float32)
+        self.ctx.check(self._lib.perks_warmnet_train_step(self.handle, nimg, ny, nx, kp, fp, up, float(lr),
+                                                          _stream(stream), loss.ctypes.data))
+        return float(loss[0])
+
+    def fit(self, k, f, u, batch: int = 16, epochs: int = 1, lr: float = 1e-3, auto_scale: bool = True,
+            seed: int = 0, stream=None) -> np.ndarray:
+        nimg, ny, nx = self._dims(k)
+        kp, fp, up = self._ptrs(k, f, u)
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        self.ctx.check(self._lib.perks_warmnet_fit(self.handle, nimg, ny, nx, kp, fp, up, int(batch), int(epochs),
+                                                   float(lr), int(bool(auto_scale)), int(seed), _stream(stream),
+                                                   losses.ctypes.data))
+        return losses[:epochs]

@@ -233,7 +233,7 @@ perks_status plan_batch(perks_batch *b, BatchKernel &k, double granularity, int 
     const int G = ctx->sm_count;  // one block per SM
     const int V = k.v;
     const int es = b->es;
-    const int S = 2 * kBatchMaxR + 1 + k.d;
+    const int S = vec_slots<kBatchMaxR, 0>() + k.d;
     const int HX = std::max(V, 2);
     const int maxw = std::min(width_cap > 0 ? width_cap : kBatchThreads * V, kBatchThreads * V);
     long long total = 0;

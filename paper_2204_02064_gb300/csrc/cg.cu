@@ -1,6 +1,7 @@
 // Host side of the CG solver: operator creation (device copies, the fp32
 // value copy, the merge-path partition computed once), the persistent solve,
 // the multi-launch baseline and the C ABI entry points perks_csr_* / perks_cg_*.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -195,8 +196,11 @@ struct perks_op {
     int *rowptr = nullptr, *col = nullptr;
     double *val = nullptr;
     float *val32 = nullptr;
-    int *part_row = nullptr, *part_ntiles = nullptr;
+    int *part_row = nullptr, *part_ntiles = nullptr;   // merge kernel: G blocks
     int2 *part_tiles = nullptr;
+    int G2 = 0;                                         // row-vector kernel: G2 blocks
+    int *part_row2 = nullptr, *part_ntiles2 = nullptr;
+    int2 *part_tiles2 = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
     double *part = nullptr;
@@ -224,7 +228,7 @@ template <typename T> perks_status dalloc(perks_context *ctx, T **p, size_t coun
 
 void free_op(perks_op *op) {
     void *ptrs[] = {op->rowptr, op->col, op->val, op->val32, op->part_row, op->part_ntiles,
-                    op->part_tiles, op->b, op->x, op->r, op->p, op->q, op->r32, op->p32,
+                    op->part_tiles, op->part_row2, op->part_ntiles2, op->part_tiles2, op->b, op->x, op->r, op->p, op->q, op->r32, op->p32,
                     op->q32, op->d32, op->part, op->trace, op->res, op->ms, op->bar, op->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -240,9 +244,10 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.col = op->col;
     a.val = op->val;
     a.val32 = op->val32;
-    a.part_row = op->part_row;
-    a.part_ntiles = op->part_ntiles;
-    a.part_tiles = op->part_tiles;
+    const bool rv = op->spmv_kind == PERKS_SPMV_ROWVEC;
+    a.part_row = rv ? op->part_row2 : op->part_row;
+    a.part_ntiles = rv ? op->part_ntiles2 : op->part_ntiles;
+    a.part_tiles = rv ? op->part_tiles2 : op->part_tiles;
     a.b = op->b;
     a.x = op->x; a.r = op->r; a.p = op->p; a.q = op->q;
     a.r32 = op->r32; a.p32 = op->p32; a.q32 = op->q32; a.d32 = op->d32;
@@ -267,15 +272,20 @@ perks_status configure(perks_op *op) {
     if (op->configured) return PERKS_OK;
     perks_context *ctx = op->ctx;
     const int smem = (int)cg_smem_bytes();
-    PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)perks_cg_kernel,
+    PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)perks_cg_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)cg_multi_spmv,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_cg_kernel,
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_cg_kernel<false>,
                                                                   kCgThreads, smem));
     if (per_sm < 1 || per_sm * ctx->sm_count < op->G)
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G);
+    int per_sm2 = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void *)perks_cg_kernel<true>,
+                                                                  kCgThreads, kCgRowvecSmem));
+    if (per_sm2 < 1 || per_sm2 * ctx->sm_count < op->G2)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G2);
     op->configured = true;
     return PERKS_OK;
 }
@@ -285,14 +295,18 @@ perks_status launch_persistent(perks_op *op, const CgArgs &a, cudaStream_t s) {
     PERKS_CUDA(ctx, cudaMemsetAsync(op->bar, 0, sizeof(unsigned long long), s));
     PERKS_CUDA(ctx, cudaMemsetAsync(op->err, 0, sizeof(DevError), s));
     void *args[] = {(void *)&a};
-    PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel, dim3(op->G),
-                                                dim3(kCgThreads), args, cg_smem_bytes(), s));
+    if (op->spmv_kind == PERKS_SPMV_ROWVEC)
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<true>, dim3(op->G2),
+                                                    dim3(kCgThreads), args, kCgRowvecSmem, s));
+    else
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<false>, dim3(op->G),
+                                                    dim3(kCgThreads), args, cg_smem_bytes(), s));
     return PERKS_OK;
 }
 
 perks_status solve_multi(perks_op *op, CgArgs a, cudaStream_t s) {
     perks_context *ctx = op->ctx;
-    const dim3 grid(op->G), block(kCgThreads);
+    const dim3 grid(op->spmv_kind == PERKS_SPMV_ROWVEC ? op->G2 : op->G), block(kCgThreads);
     const size_t smem = cg_smem_bytes();
     a.trace_cap = op->trace_cap;
     cg_multi_spmv<<<grid, block, smem, s>>>(a, op->x, op->q, nullptr, nullptr, nullptr);
@@ -348,7 +362,7 @@ perks_status read_result(perks_op *op, cudaStream_t s, perks_cg_stats *stats) {
         stats->outer_iterations = r.outer;
         stats->true_rel_residual = r.bb > 0 ? sqrt(r.true_rr / r.bb) : sqrt(r.true_rr);
         stats->status = st;
-        stats->grid_blocks = op->G;
+        stats->grid_blocks = op->spmv_kind == PERKS_SPMV_ROWVEC ? op->G2 : op->G;
         stats->threads_per_block = kCgThreads;
         const double vbytes = op->last_mode == PERKS_CG_FP32_IR ? 4.0 : 8.0;
         // A (values + column indices + row pointers) once, the gathered vector
@@ -443,14 +457,21 @@ extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t 
         }
     }
     const int G = op->G;
+    op->G2 = 2 * ctx->sm_count;
+    const int G2 = op->G2;
     OPCHK(dalloc(ctx, &op->part_row, (size_t)G + 1));
     OPCHK(dalloc(ctx, &op->part_ntiles, (size_t)G));
     OPCHK(dalloc(ctx, &op->part_tiles, (size_t)G * (kCgMaxTiles + 1)));
+    OPCHK(dalloc(ctx, &op->part_row2, (size_t)G2 + 1));
+    OPCHK(dalloc(ctx, &op->part_ntiles2, (size_t)G2));
+    OPCHK(dalloc(ctx, &op->part_tiles2, (size_t)G2 * (kCgMaxTiles + 1)));
     int *overflow = nullptr;
     OPCHK(dalloc(ctx, &overflow, 1));
     OPCUDA(cudaMemset(overflow, 0, sizeof(int)));
     cg_partition_kernel<<<G, 256>>>(op->rowptr, n, nnz, G, op->part_row, op->part_ntiles, op->part_tiles,
                                     overflow);
+    cg_partition_kernel<<<G2, 256>>>(op->rowptr, n, nnz, G2, op->part_row2, op->part_ntiles2, op->part_tiles2,
+                                     overflow);
     OPCUDA(cudaGetLastError());
     int ov = 0;
     OPCUDA(cudaMemcpy(&ov, overflow, sizeof(int), cudaMemcpyDeviceToHost));
@@ -469,7 +490,7 @@ extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t 
     OPCHK(dalloc(ctx, &op->p32, (size_t)n));
     OPCHK(dalloc(ctx, &op->q32, (size_t)n));
     OPCHK(dalloc(ctx, &op->d32, (size_t)n));
-    OPCHK(dalloc(ctx, &op->part, (size_t)2 * G));
+    OPCHK(dalloc(ctx, &op->part, (size_t)2 * std::max(G, G2)));
     OPCHK(dalloc(ctx, &op->trace, (size_t)3 * op->trace_cap));
     OPCHK(dalloc(ctx, &op->res, 1));
     OPCHK(dalloc(ctx, &op->ms, 1));

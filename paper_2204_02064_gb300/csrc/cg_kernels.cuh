@@ -26,6 +26,8 @@
 // decisions (convergence, breakdown) without further communication.
 #pragma once
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace perks {
@@ -412,6 +414,7 @@ template <typename V>
 __device__ __forceinline__ double spmv_any(const CgArgs &a, const CgSmem &s, const CgSlice &sl, const V *gval,
                                            const V *vin, V *vout, const V *dotv) {
     if (a.spmv_kind == 0 && !sl.cached) return spmv_block_vec<V>(a, sl, gval, vin, vout, dotv, s.red);
+    if (s.bufs == nullptr) return 0.0;  // row-vector kernel: never reached (spmv_kind is 0)
     return spmv_block<V>(a, s, sl, gval, vin, vout, dotv);
 }
 
@@ -419,10 +422,23 @@ __device__ __forceinline__ bool cg_sync(const CgArgs &a, unsigned long long &epo
     return grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns);
 }
 
+// Shared memory of the row-vector kernel: the reduction scratch only.
+constexpr size_t kCgRowvecSmem = 1024;
+
 // Persistent CG (mode FP64 / FP32_IR) or a single SpMV (mode SPMV).
-__global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_constant__ CgArgs a) {
+// ROWVEC: row-vector SpMV only, 1 KB of shared memory and at most 64
+// registers, so two blocks share an SM (twice the loads in flight); otherwise
+// the merge-based SpMV with its staged tiles, one block per SM.
+template <bool ROWVEC>
+__global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(const __grid_constant__ CgArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const CgSmem s = carve_cg_smem(smem_raw);
+    CgSmem s;
+    if constexpr (ROWVEC) {
+        std::memset(&s, 0, sizeof(s));
+        s.red = reinterpret_cast<double *>(smem_raw);
+    } else {
+        s = carve_cg_smem(smem_raw);
+    }
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
     unsigned long long epoch = 0;
 
@@ -431,10 +447,13 @@ __global__ void __launch_bounds__(kCgThreads, 1) perks_cg_kernel(const __grid_co
     sl.r1 = a.part_row[blk + 1];
     sl.jb = a.rowptr[sl.r0];
     sl.T = a.part_ntiles[blk];
-    for (int u = tid; u <= sl.T; u += blockDim.x)
-        s.tiles[u] = a.part_tiles[(long long)blk * (kCgMaxTiles + 1) + u];
-    __syncthreads();
-    sl.cached = a.allow_cache && a.mode == CGK_FP64 && sl.T <= kCgBufs;
+    sl.cached = false;
+    if constexpr (!ROWVEC) {
+        for (int u = tid; u <= sl.T; u += blockDim.x)
+            s.tiles[u] = a.part_tiles[(long long)blk * (kCgMaxTiles + 1) + u];
+        __syncthreads();
+        sl.cached = a.allow_cache && a.mode == CGK_FP64 && sl.T <= kCgBufs;
+    }
     if (sl.cached) {
         for (int u = 0; u < sl.T; ++u) stage_tile<double, false>(a, s, sl, u, a.val, tile_buf<double>(s, u));
         __syncthreads();

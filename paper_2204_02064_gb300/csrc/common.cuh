@@ -95,15 +95,28 @@ struct DevError {
     int pad;
 };
 
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 // Grid-wide barrier over `nblocks` co-resident blocks (a cooperative launch
 // guarantees co-residency).  `counter` is a monotone 64-bit arrival count,
 // zeroed before the launch; the e-th barrier (e = 1, 2, ...) completes when
-// the count reaches e * nblocks.  Thread 0 of each block arrives with a
-// release reduction and waits with acquire loads, then the block is released
-// by __syncthreads.  The wait is bounded by `timeout_ns` of %globaltimer: on
-// expiry (or when another block has already failed) the block records
-// BARRIER_TIMEOUT and the call returns false in every thread, so the caller
-// leaves its loop and the whole grid winds down without hanging.
+// the count reaches e * nblocks.  After __syncthreads, thread 0 arrives with
+// a gpu-scope release reduction (cumulative over the block's writes ordered
+// before it by the bar.sync), polls with relaxed loads and, once the count is
+// reached, issues one acquire fence; the closing __syncthreads orders every
+// thread's later accesses after it.  No full (sc) fence is needed.  The wait
+// is bounded by `timeout_ns` of %globaltimer: on expiry (or when another
+// block has already failed) the block records BARRIER_TIMEOUT and the call
+// returns false in every thread, so the caller leaves its loop and the whole
+// grid winds down without hanging.
 __device__ __forceinline__ bool grid_barrier(unsigned long long *counter, unsigned nblocks,
                                              unsigned long long &epoch, DevError *err,
                                              long long timeout_ns) {
@@ -113,14 +126,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *counter, unsign
         int fail = 0;
         ++epoch;
         const unsigned long long target = epoch * (unsigned long long)nblocks;
-        __threadfence();
         red_release_gpu_add(counter, 1ull);
-        const uint64_t t0 = global_timer_ns();
-        unsigned spins = 0;
-        while (ld_acquire_gpu(counter) < target) {
-            if ((++spins & 63u) == 0) {
-                if (ld_relaxed_gpu(&err->code) != 0) { fail = 1; break; }
-                if ((long long)(global_timer_ns() - t0) > timeout_ns) {
+        if (ld_relaxed_gpu_u64(counter) < target) {
+            const uint64_t t0 = global_timer_ns();
+            unsigned spins = 0;
+            for (;;) {
+                if (timeout_ns == 0) {  // test hook: give up at the first wait
                     if (atomicCAS(&err->code, 0, PERKS_ERR_BARRIER_TIMEOUT) == 0) {
                         err->block = blockIdx.x;
                         err->epoch = (int)epoch;
@@ -128,17 +139,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *counter, unsign
                     fail = 1;
                     break;
                 }
-            }
-            if (timeout_ns == 0) {  // test hook: give up at the first wait
-                if (atomicCAS(&err->code, 0, PERKS_ERR_BARRIER_TIMEOUT) == 0) {
-                    err->block = blockIdx.x;
-                    err->epoch = (int)epoch;
+                if (ld_relaxed_gpu_u64(counter) >= target) break;
+                if ((++spins & 255u) == 0) {
+                    if (ld_relaxed_gpu(&err->code) != 0) { fail = 1; break; }
+                    if ((long long)(global_timer_ns() - t0) > timeout_ns) {
+                        if (atomicCAS(&err->code, 0, PERKS_ERR_BARRIER_TIMEOUT) == 0) {
+                            err->block = blockIdx.x;
+                            err->epoch = (int)epoch;
+                        }
+                        fail = 1;
+                        break;
+                    }
                 }
-                fail = 1;
-                break;
             }
         }
-        __threadfence();
+        fence_acquire_gpu();
         s_fail = fail;
     }
     __syncthreads();

@@ -1,0 +1,350 @@
+// Batched variable-coefficient Poisson: -div(k grad u) = f on nx*ny grids
+// (5-point finite volumes, h = 1, face coefficient = harmonic mean of the two
+// cells' k, Dirichlet 0 through a ghost cell carrying the boundary cell's k),
+// solved by CG (the Sec. 2.2.2 recurrence) as ONE persistent launch.
+//
+// Problems are independent, so the batch needs no grid barrier: each block
+// owns one problem at a time (blocks pull problems from an atomic counter),
+// keeps its scalars and partial sums on chip and runs that problem's whole
+// CG loop -- SpMV (matrix-free, from precomputed face coefficients), dot
+// products and axpys -- with block-level reductions only.  The true residual
+// is recomputed in fp64 on exit and CG restarts while it is above tolerance.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "common.cuh"
+
+using namespace perks;
+
+namespace {
+
+constexpr int kPoiThreads = 512;
+
+struct PoissonArgs {
+    int nx, ny, nprob;
+    long long n;                 // cells per problem
+    const double *fx;            // [prob][ny][nx+1] x-face coefficients
+    const double *fy;            // [prob][ny+1][nx] y-face coefficients
+    const double *b;             // [prob][n]
+    double *x, *r, *p, *q;       // [prob][n]
+    double rtol;
+    int max_iter;
+    int max_restarts;
+    int *queue;                  // next problem to take
+    int *iters;                  // [prob] recurrence iterations
+    double *true_rel;            // [prob] ||b - A x|| / ||b||
+    int *status;                 // [prob]
+};
+
+__global__ void poisson_faces_kernel(const double *__restrict__ k, int nx, int ny, long long total_cells,
+                                     double *fx, double *fy) {
+    // one thread per face; x-faces: (nx+1)*ny per problem, y-faces: nx*(ny+1)
+    const long long nfx = (long long)(nx + 1) * ny, nfy = (long long)nx * (ny + 1);
+    const long long nprob = total_cells / ((long long)nx * ny);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nprob * (nfx + nfy); t += stride) {
+        const long long pb = t / (nfx + nfy), u = t % (nfx + nfy);
+        const double *kp = k + pb * (long long)nx * ny;
+        if (u < nfx) {
+            const int j = (int)(u / (nx + 1)), i = (int)(u % (nx + 1));
+            double f;
+            if (i == 0) f = kp[(long long)j * nx];
+            else if (i == nx) f = kp[(long long)j * nx + nx - 1];
+            else {
+                const double a = kp[(long long)j * nx + i - 1], c = kp[(long long)j * nx + i];
+                f = 2.0 * a * c / (a + c);
+            }
+            fx[pb * nfx + u] = f;
+        } else {
+            const long long v = u - nfx;
+            const int j = (int)(v / nx), i = (int)(v % nx);
+            double f;
+            if (j == 0) f = kp[i];
+            else if (j == ny) f = kp[(long long)(ny - 1) * nx + i];
+            else {
+                const double a = kp[(long long)(j - 1) * nx + i], c = kp[(long long)j * nx + i];
+                f = 2.0 * a * c / (a + c);
+            }
+            fy[pb * nfy + v] = f;
+        }
+    }
+}
+
+// (A v)_c for cell c = (i, j) of one problem.
+__device__ __forceinline__ double apply_cell(const double *__restrict__ fxp, const double *__restrict__ fyp,
+                                             const double *__restrict__ v, int nx, int ny, int i, int j) {
+    const long long c = (long long)j * nx + i;
+    const double fw = fxp[(long long)j * (nx + 1) + i], fe = fxp[(long long)j * (nx + 1) + i + 1];
+    const double fs = fyp[(long long)j * nx + i], fn = fyp[(long long)(j + 1) * nx + i];
+    const double vc = v[c];
+    double s = (fw + fe) + (fs + fn);
+    double acc = s * vc;
+    if (i > 0) acc = fma(-fw, v[c - 1], acc);
+    if (i + 1 < nx) acc = fma(-fe, v[c + 1], acc);
+    if (j > 0) acc = fma(-fs, v[c - nx], acc);
+    if (j + 1 < ny) acc = fma(-fn, v[c + nx], acc);
+    return acc;
+}
+
+// Visits every cell of one problem, rows outer, threads across a row.
+#define FOR_CELLS(nx, ny, i, j, c)                                  \
+    for (int j = 0; j < (ny); ++j)                                  \
+        for (int i = threadIdx.x; i < (nx); i += blockDim.x)        \
+            if (const long long c = (long long)j * (nx) + i; true)
+
+__device__ __forceinline__ double bsum(double v, double *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+        t = warp_sum(t);
+        if (l == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+__global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const __grid_constant__ PoissonArgs a) {
+    __shared__ double red[33];
+    __shared__ int s_prob;
+    const int nx = a.nx, ny = a.ny;
+    const long long n = a.n;
+    for (;;) {
+        if (threadIdx.x == 0) s_prob = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int pb = s_prob;
+        __syncthreads();
+        if (pb >= a.nprob) break;
+        const double *fxp = a.fx + (long long)pb * (nx + 1) * ny;
+        const double *fyp = a.fy + (long long)pb * nx * (ny + 1);
+        const double *b = a.b + pb * n;
+        double *x = a.x + pb * n, *r = a.r + pb * n, *p = a.p + pb * n, *q = a.q + pb * n;
+        // r = b - A x, p = r
+        double bb = 0.0, rr = 0.0;
+        FOR_CELLS(nx, ny, i, j, c) {
+            const double ri = b[c] - apply_cell(fxp, fyp, x, nx, ny, i, j);
+            r[c] = ri;
+            p[c] = ri;
+            bb = fma(b[c], b[c], bb);
+            rr = fma(ri, ri, rr);
+        }
+        bb = bsum(bb, red);
+        rr = bsum(rr, red);
+        const double tol2 = a.rtol * a.rtol * bb;
+        int it = 0, status = PERKS_ERR_NOT_CONVERGED;
+        for (int restart = 0;; ++restart) {
+            if (rr <= tol2) { status = PERKS_OK; break; }
+            bool converged = false;
+            while (it < a.max_iter) {
+                double pq = 0.0;
+                FOR_CELLS(nx, ny, i, j, c) {
+                    const double qc = apply_cell(fxp, fyp, p, nx, ny, i, j);
+                    q[c] = qc;
+                    pq = fma(p[c], qc, pq);
+                }
+                pq = bsum(pq, red);
+                if (!(pq > 0.0) || !isfinite(pq)) { status = PERKS_ERR_BREAKDOWN; break; }
+                const double alpha = rr / pq;
+                double rn = 0.0;
+                for (long long c = threadIdx.x; c < n; c += blockDim.x) {
+                    x[c] = fma(alpha, p[c], x[c]);
+                    const double ri = fma(-alpha, q[c], r[c]);
+                    r[c] = ri;
+                    rn = fma(ri, ri, rn);
+                }
+                rn = bsum(rn, red);
+                const double beta = rn / rr;
+                for (long long c = threadIdx.x; c < n; c += blockDim.x) p[c] = fma(beta, p[c], r[c]);
+                __syncthreads();
+                rr = rn;
+                ++it;
+                if (rr <= tol2) { converged = true; break; }
+            }
+            if (status == PERKS_ERR_BREAKDOWN) break;
+            double tr = 0.0;
+            FOR_CELLS(nx, ny, i, j, c) {
+                const double ri = b[c] - apply_cell(fxp, fyp, x, nx, ny, i, j);
+                r[c] = ri;
+                tr = fma(ri, ri, tr);
+            }
+            rr = bsum(tr, red);
+            if (rr <= tol2) { status = PERKS_OK; break; }
+            if (!converged || restart >= a.max_restarts) break;
+            for (long long c = threadIdx.x; c < n; c += blockDim.x) p[c] = r[c];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            a.iters[pb] = it;
+            a.true_rel[pb] = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+            a.status[pb] = status;
+        }
+        __syncthreads();
+    }
+}
+
+// y = A v for every problem (one launch; for tests).
+__global__ void poisson_apply_kernel(const __grid_constant__ PoissonArgs a, const double *v, double *y) {
+    const long long total = (long long)a.nprob * a.n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long pb = t / a.n, c = t % a.n;
+        const double *fxp = a.fx + pb * (a.nx + 1) * a.ny;
+        const double *fyp = a.fy + pb * a.nx * (a.ny + 1);
+        y[t] = apply_cell(fxp, fyp, v + pb * a.n, a.nx, a.ny, (int)(c % a.nx), (int)(c / a.nx));
+    }
+}
+
+}  // namespace
+
+struct perks_poisson {
+    perks_context *ctx = nullptr;
+    int nx = 0, ny = 0, nprob = 0;
+    long long n = 0;
+    double *fx = nullptr, *fy = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    int *queue = nullptr, *iters = nullptr, *status = nullptr;
+    double *true_rel = nullptr;
+};
+
+namespace {
+void free_poisson(perks_poisson *P) {
+    void *ptrs[] = {P->fx, P->fy, P->b, P->x, P->r, P->p, P->q, P->queue, P->iters, P->status, P->true_rel};
+    for (void *v : ptrs) if (v) cudaFree(v);
+}
+
+PoissonArgs poisson_args(perks_poisson *P) {
+    PoissonArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = P->nx; a.ny = P->ny; a.nprob = P->nprob; a.n = P->n;
+    a.fx = P->fx; a.fy = P->fy; a.b = P->b; a.x = P->x; a.r = P->r; a.p = P->p; a.q = P->q;
+    a.queue = P->queue; a.iters = P->iters; a.true_rel = P->true_rel; a.status = P->status;
+    return a;
+}
+}  // namespace
+
+extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int32_t ny, int32_t nprob,
+                                             const double *k, int on_device, perks_poisson **out) {
+    if (!ctx) return PERKS_ERR_INVALID_ARG;
+    if (!out || !k || nx < 1 || ny < 1 || nprob < 1)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "poisson_create: bad arguments");
+    *out = nullptr;
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    auto *P = new perks_poisson();
+    P->ctx = ctx;
+    P->nx = nx; P->ny = ny; P->nprob = nprob;
+    P->n = (long long)nx * ny;
+    const size_t vb = sizeof(double) * (size_t)P->n * nprob;
+    const size_t fxb = sizeof(double) * (size_t)(nx + 1) * ny * nprob;
+    const size_t fyb = sizeof(double) * (size_t)nx * (ny + 1) * nprob;
+    double *kd = nullptr;
+    cudaError_t e = cudaSuccess;
+    void **bufs[] = {(void **)&P->b, (void **)&P->x, (void **)&P->r, (void **)&P->p, (void **)&P->q};
+    for (void **bp : bufs) if (e == cudaSuccess) e = cudaMalloc(bp, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&P->fx, fxb);
+    if (e == cudaSuccess) e = cudaMalloc(&P->fy, fyb);
+    if (e == cudaSuccess) e = cudaMalloc(&P->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&P->iters, sizeof(int) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc(&P->status, sizeof(int) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc(&P->true_rel, sizeof(double) * nprob);
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMalloc(&kd, vb);
+        if (e == cudaSuccess) e = cudaMemcpy(kd, k, vb, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        if (kd) cudaFree(kd);
+        free_poisson(P);
+        delete P;
+        return cuda_fail(ctx, e, "poisson_create");
+    }
+    poisson_faces_kernel<<<1024, 256>>>(on_device ? k : kd, nx, ny, P->n * nprob, P->fx, P->fy);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (kd) cudaFree(kd);
+    if (e != cudaSuccess) { free_poisson(P); delete P; return cuda_fail(ctx, e, "poisson_create: faces"); }
+    *out = P;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_destroy(perks_poisson *P) {
+    if (!P) return PERKS_OK;
+    if (P->ctx) cudaSetDevice(P->ctx->device);
+    free_poisson(P);
+    delete P;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_apply(perks_poisson *P, const double *v, double *y, perks_stream stream) {
+    if (!P) return PERKS_ERR_INVALID_ARG;
+    if (!v || !y) return fail(P->ctx, PERKS_ERR_INVALID_ARG, "poisson_apply: NULL vector");
+    perks_status rc = use_device(P->ctx);
+    if (rc) return rc;
+    poisson_apply_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(poisson_args(P), v, y);
+    PERKS_CUDA(P->ctx, cudaGetLastError());
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, double *x, double rtol,
+                                            int32_t max_iter, perks_stream stream, perks_poisson_stats *stats) {
+    if (!P) return PERKS_ERR_INVALID_ARG;
+    perks_context *ctx = P->ctx;
+    if (!b || !x || !(rtol >= 0) || max_iter < 0) return fail(ctx, PERKS_ERR_INVALID_ARG, "poisson_solve: bad arguments");
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = sizeof(double) * (size_t)P->n * P->nprob;
+    PERKS_CUDA(ctx, cudaMemcpyAsync(P->b, b, vb, cudaMemcpyDeviceToDevice, s));
+    PERKS_CUDA(ctx, cudaMemcpyAsync(P->x, x, vb, cudaMemcpyDeviceToDevice, s));
+    PERKS_CUDA(ctx, cudaMemsetAsync(P->queue, 0, sizeof(int), s));
+    PoissonArgs a = poisson_args(P);
+    a.rtol = rtol;
+    a.max_iter = max_iter;
+    a.max_restarts = 8;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_poisson_cg_kernel,
+                                                                  kPoiThreads, 0));
+    const int grid = std::max(1, std::min(P->nprob, per_sm * ctx->sm_count));
+    perks_poisson_cg_kernel<<<grid, kPoiThreads, 0, s>>>(a);
+    PERKS_CUDA(ctx, cudaGetLastError());
+    PERKS_CUDA(ctx, cudaMemcpyAsync(x, P->x, vb, cudaMemcpyDeviceToDevice, s));
+    if (!stats) return PERKS_OK;
+    PERKS_CUDA(ctx, cudaStreamSynchronize(s));
+    int32_t *it_out = stats->iterations;
+    double *tr_out = stats->true_rel_residual;
+    const int32_t cap = stats->capacity;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = it_out;
+    stats->true_rel_residual = tr_out;
+    stats->capacity = cap;
+    stats->problems = P->nprob;
+    stats->grid_blocks = grid;
+    int *it = new int[P->nprob];
+    int *st = new int[P->nprob];
+    double *tr = new double[P->nprob];
+    cudaMemcpy(it, P->iters, sizeof(int) * P->nprob, cudaMemcpyDeviceToHost);
+    cudaMemcpy(st, P->status, sizeof(int) * P->nprob, cudaMemcpyDeviceToHost);
+    cudaMemcpy(tr, P->true_rel, sizeof(double) * P->nprob, cudaMemcpyDeviceToHost);
+    perks_status worst = PERKS_OK;
+    long long sum_it = 0;
+    for (int i = 0; i < P->nprob; ++i) {
+        sum_it += it[i];
+        stats->max_iterations = std::max(stats->max_iterations, it[i]);
+        stats->max_true_rel_residual = std::max(stats->max_true_rel_residual, tr[i]);
+        if (st[i] != PERKS_OK && worst == PERKS_OK) worst = st[i];
+        if (stats->iterations && i < stats->capacity) {
+            stats->iterations[i] = it[i];
+            if (stats->true_rel_residual) stats->true_rel_residual[i] = tr[i];
+        }
+    }
+    stats->mean_iterations = (double)sum_it / P->nprob;
+    delete[] it;
+    delete[] st;
+    delete[] tr;
+    if (worst != PERKS_OK) return fail(ctx, worst, "poisson_solve: a problem did not converge (status %d)", worst);
+    return PERKS_OK;
+}

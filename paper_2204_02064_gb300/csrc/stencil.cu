@@ -90,9 +90,15 @@ std::vector<KernelEntry> &registry() {
         table.push_back(entry<double, S3d13, 1024, 0>(PERKS_F64, SH_3D13));
         table.push_back(entry<float, S3d13, 1024, 0>(PERKS_F32, SH_3D13));
         // vectorised kernels: x extent a multiple of V (16-byte vectors)
-        register_vec_f64(table);
-        register_vec_f32(table);
-        register_vec_bf16(table);
+        register_vec_f64_core(table);
+        register_vec_f64_box2d(table);
+        register_vec_f64_box3d(table);
+        register_vec_f32_core(table);
+        register_vec_f32_box2d(table);
+        register_vec_f32_box3d(table);
+        register_vec_bf16_core(table);
+        register_vec_bf16_box2d(table);
+        register_vec_bf16_box3d(table);
     }
     return table;
 }
@@ -203,7 +209,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     }
     const int R = sh.radius;
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
-    const int S = 2 * RZ + 1 + k.d;
+    const int S = 2 * RZ + 1 + k.d + (k.v > 1 ? 1 : 0);  // the vector kernel pairs planes (one more slot)
     const int es = st->es;
     const int V = k.v;
     const int HX = V > 1 ? std::max(V, 2) : RX;  // ring pad columns on each side

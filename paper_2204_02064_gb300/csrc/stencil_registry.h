@@ -32,8 +32,14 @@ struct KernelEntry {
     int smem_budget = 0;    // dynamic shared memory available per block
 };
 
-void register_vec_f64(std::vector<KernelEntry> &out);
-void register_vec_f32(std::vector<KernelEntry> &out);
-void register_vec_bf16(std::vector<KernelEntry> &out);
+void register_vec_f64_core(std::vector<KernelEntry> &out);
+void register_vec_f64_box2d(std::vector<KernelEntry> &out);
+void register_vec_f64_box3d(std::vector<KernelEntry> &out);
+void register_vec_f32_core(std::vector<KernelEntry> &out);
+void register_vec_f32_box2d(std::vector<KernelEntry> &out);
+void register_vec_f32_box3d(std::vector<KernelEntry> &out);
+void register_vec_bf16_core(std::vector<KernelEntry> &out);
+void register_vec_bf16_box2d(std::vector<KernelEntry> &out);
+void register_vec_bf16_box3d(std::vector<KernelEntry> &out);
 
 }  // namespace perks

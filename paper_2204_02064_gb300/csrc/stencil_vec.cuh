@@ -219,86 +219,6 @@ __device__ __forceinline__ void set_vec(T *d, T v) {
     *reinterpret_cast<VecOf<T, V> *>(d) = x;
 }
 
-template <typename T, class SH, int V, int ZR, bool REG, bool PER_STEP>
-__device__ __forceinline__ void vfill_plane(const PersistentArgs &a, const VecPlan &tp, int p, T *sl,
-                                            const T *fs, const T *hs, const T *smc,
-                                            const VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
-    using VT = VecOf<T, V>;
-    using PT = PairOf<T>;
-    const T bnd = ScalarOps<T>::bnd(a);
-    const int gz = tp.z0 + p;
-    const bool in_z = gz >= 0 && gz < a.Z;
-    const bool inside = p >= 0 && p < tp.tz;
-    if (tp.own) {
-        T *d = sl + tp.sidx;
-        if (!in_z) {
-            set_vec<T, V>(d, bnd);
-        } else if (!inside || PER_STEP) {
-            copy_vec<T, V>(d, fs + (long long)gz * a.XY + tp.gxy);
-        } else {
-            bool done = false;
-            if constexpr (REG && ZR > 0) {
-                if (p >= 0 && p < ZR) {
-                    *reinterpret_cast<VT *>(d) = regc[p < 0 ? 0 : (p < ZR ? p : 0)];
-                    done = true;
-                }
-            }
-            if (!done) {
-                if (p < ZR + a.zs)
-                    *reinterpret_cast<VT *>(d) =
-                        *reinterpret_cast<const VT *>(smc + ((long long)(p - ZR) * a.ncol + threadIdx.x * V));
-                else
-                    copy_vec<T, V>(d, fs + (long long)gz * a.XY + tp.gxy);
-            }
-        }
-    }
-    if (tp.duty != DUTY_NONE && (inside || SH::BOX)) {
-        T *d = sl + tp.dsidx;
-        const bool vec = tp.duty == DUTY_FIELD_VEC || tp.duty == DUTY_BND_VEC;
-        if (!in_z || tp.duty == DUTY_BND_VEC || tp.duty == DUTY_BND_PAIR) {
-            if (vec) set_vec<T, V>(d, bnd);
-            else { PT x; x.v[0] = bnd; x.v[1] = bnd; *reinterpret_cast<PT *>(d) = x; }
-        } else if (tp.duty == DUTY_FIELD_VEC) {
-            copy_vec<T, V>(d, fs + (long long)gz * a.XY + tp.dgxy);
-        } else if (tp.duty == DUTY_XPAIR && inside && !PER_STEP) {
-            cp_async<sizeof(T) * 2>(d, hs + tp.dface + (long long)p * a.tymax * 2);
-        } else {
-            cp_async<sizeof(T) * 2>(d, fs + (long long)gz * a.XY + tp.dgxy);
-        }
-    }
-}
-
-template <typename T, class SH, int V, int ZR, bool REG>
-__device__ __forceinline__ void vstore(const PersistentArgs &a, const VecPlan &tp, int z, const VecOf<T, V> &v,
-                                       bool last, T *fd, T *hd, T *smc, VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1],
-                                       bool per_step) {
-    using VT = VecOf<T, V>;
-    using PT = PairOf<T>;
-    constexpr int RZ = SH::RZ;
-    bool cached = false;
-    if (!per_step) {
-        if constexpr (REG && ZR > 0) {
-            if (z < ZR) { regc[z < ZR ? z : 0] = v; cached = true; }
-        }
-        if (!cached && z < ZR + a.zs) {
-            *reinterpret_cast<VT *>(smc + ((long long)(z - ZR) * a.ncol + threadIdx.x * V)) = v;
-            cached = true;
-        }
-    }
-    const bool zshell = (z < RZ && tp.has_b) || (z >= tp.tz - RZ && tp.has_t);
-    if (last || !cached || tp.field_shell || zshell)
-        *reinterpret_cast<VT *>(fd + (long long)(tp.z0 + z) * a.XY + tp.gxy) = v;
-    const long long fz = (long long)z * a.tymax * 2;
-    if (tp.wface) {
-        PT x; x.v[0] = v.v[0]; x.v[1] = v.v[V >= 2 ? 1 : 0];
-        *reinterpret_cast<PT *>(hd + tp.wface_off + fz) = x;
-    }
-    if (tp.eface) {
-        PT x; x.v[0] = v.v[V >= 2 ? V - 2 : 0]; x.v[1] = v.v[V - 1];
-        *reinterpret_cast<PT *>(hd + tp.eface_off + fz) = x;
-    }
-}
-
 // Loads R cells (1 or 2) ending just left of / starting just right of a vector.
 template <typename T, int N>
 __device__ __forceinline__ void load_cells(const T *p, T (&out)[N > 0 ? N : 1]) {
@@ -311,73 +231,9 @@ __device__ __forceinline__ void load_cells(const T *p, T (&out)[N > 0 ? N : 1]) 
     }
 }
 
-template <typename T, class SH, int V, int ZR, int D, bool REG, bool PER_STEP>
-__device__ __forceinline__ void vplane_iteration(const PersistentArgs &a, const VecPlan &tp, int z, int slo,
-                                                 bool last, T *ring, const T *fs, const T *hs, T *fd, T *hd,
-                                                 T *smc, VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
-    using A = typename ScalarOps<T>::A;
-    using VT = VecOf<T, V>;
-    using RW = RowsOf<SH>;
-    constexpr int RZ = SH::RZ;
-    constexpr int R = SH::R;
-    constexpr int S = 2 * RZ + 1 + D;
-    constexpr int NR = RW::count();
-    cp_async_wait<D - 1>();
-    __syncthreads();
-    if (tp.own) {
-        // row segments: [R left cells | V own-column cells | R right cells]
-        A seg[NR][V + 2 * R];
-        static_for<0, NR>([&](auto RI) {
-            constexpr int r = decltype(RI)::value;
-            constexpr int dzr = RW::dz(r), dyr = RW::dy(r);
-            constexpr bool left = RW::minx(r) < 0, right = RW::maxx(r) > 0;
-            int s = slo + RZ + dzr;
-            s = s >= S ? s - S : s;
-            const T *rp = ring + (long long)s * a.plane + tp.sidx + dyr * a.PW;
-            const VT c = *reinterpret_cast<const VT *>(rp);
-            static_for<0, V>([&](auto JI) {
-                constexpr int j = decltype(JI)::value;
-                seg[r][R + j] = to_acc(c.v[j]);
-            });
-            if constexpr (left) {
-                T l[R];
-                load_cells<T, R>(rp - R, l);
-                static_for<0, R>([&](auto JI) {
-                    constexpr int j = decltype(JI)::value;
-                    seg[r][j] = to_acc(l[j]);
-                });
-            }
-            if constexpr (right) {
-                T rr[R];
-                load_cells<T, R>(rp + V, rr);
-                static_for<0, R>([&](auto JI) {
-                    constexpr int j = decltype(JI)::value;
-                    seg[r][R + V + j] = to_acc(rr[j]);
-                });
-            }
-        });
-        VT out;
-        static_for<0, V>([&](auto JI) {
-            constexpr int j = decltype(JI)::value;
-            A acc = A(0);
-            static_for<0, SH::NPTS>([&](auto II) {
-                constexpr int i = decltype(II)::value;
-                constexpr int r = RW::row_of(i);
-                constexpr int col = R + j + SH::dx(i);
-                acc = fma(ScalarOps<T>::w(a, i), seg[r][col], acc);
-            });
-            out.v[j] = from_acc<T>(acc);
-        });
-        vstore<T, SH, V, ZR, REG>(a, tp, z, out, last, fd, hd, smc, regc, PER_STEP);
-    }
-    const int q = z + RZ + D;
-    if (q < tp.tz + RZ) {
-        int s = slo + 2 * RZ + D;
-        s = s >= S ? s - S : s;
-        vfill_plane<T, SH, V, ZR, REG, PER_STEP>(a, tp, q, ring + (long long)s * a.plane, fs, hs, smc, regc);
-    }
-    cp_async_commit();
-}
+// Ring slots of the vectorised kernel: planes z-RZ..z+1+RZ are read by a
+// paired iteration while two more are filled, D planes ahead.
+template <int RZ, int D> __host__ __device__ constexpr int vec_slots() { return 2 * RZ + 2 + D; }
 
 // Where a plane's own-column values come from (fill) or go to (store).
 enum PlaneClass : int { PC_REG = 0, PC_SMEM = 1, PC_GLOBAL = 2, PC_HALO = 3, PC_NONE = 4 };
@@ -433,20 +289,19 @@ __device__ __forceinline__ void vfill_fast(const PersistentArgs &a, const VecPla
     }
 }
 
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
-__device__ __forceinline__ void vplane_fast(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
-                                            T *ring, StepPtrs<T> &sp, T *smc,
-                                            VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
+// Computes plane z (ring slot of plane z-RZ = slo) and stores it.
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE>
+__device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const VecPlan &tp, int z, int slo, bool last,
+                                               const T *ring, StepPtrs<T> &sp, T *smc,
+                                               VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     using A = typename ScalarOps<T>::A;
     using VT = VecOf<T, V>;
     using PT = PairOf<T>;
     using RW = RowsOf<SH>;
     constexpr int RZ = SH::RZ;
     constexpr int R = SH::R;
-    constexpr int S = 2 * RZ + 1 + D;
+    constexpr int S = vec_slots<RZ, D>();
     constexpr int NR = RW::count();
-    cp_async_wait<D - 1>();
-    __syncthreads();
     if (tp.own) {
         A seg[NR][V + 2 * R];
         static_for<0, NR>([&](auto RI) {
@@ -490,7 +345,6 @@ __device__ __forceinline__ void vplane_fast(const PersistentArgs &a, const VecPl
             });
             out.v[j] = from_acc<T>(acc);
         });
-        // store
         bool to_field;
         if (STORE == PC_REG) {
             if constexpr (ZR > 0) regc[z < ZR ? z : 0] = out;
@@ -516,24 +370,62 @@ __device__ __forceinline__ void vplane_fast(const PersistentArgs &a, const VecPl
     sp.store_own += a.XY;
     sp.face_dst_w += 2 * a.tymax;
     sp.face_dst_e += 2 * a.tymax;
-    {
-        int s = slo + 2 * RZ + D;
-        s = s >= S ? s - S : s;
-        vfill_fast<T, SH, V, ZR, PER_STEP, FILL>(a, tp, z + RZ + D, ring + s * a.plane, sp, smc, regc);
-    }
+}
+
+// Starts the copy of plane q (= z + RZ + D) into its slot; one cp.async group.
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int FILL>
+__device__ __forceinline__ void vfill_next(const PersistentArgs &a, const VecPlan &tp, int q, int slo_q, T *ring,
+                                           StepPtrs<T> &sp, const T *smc,
+                                           const VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
+    constexpr int S = vec_slots<SH::RZ, D>();
+    int s = slo_q;
+    s = s >= S ? s - S : s;
+    vfill_fast<T, SH, V, ZR, PER_STEP, FILL>(a, tp, q, ring + s * a.plane, sp, smc, regc);
     sp.fill_own += a.XY;
     sp.fill_duty += a.XY;
     sp.face_src += 2 * a.tymax;
     cp_async_commit();
+}
+
+// One plane per barrier.
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
+__device__ __forceinline__ void vplane_fast(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
+                                            T *ring, StepPtrs<T> &sp, T *smc,
+                                            VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
+    constexpr int RZ = SH::RZ;
+    constexpr int S = vec_slots<RZ, D>();
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z, slo, last, ring, sp, smc, regc);
+    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + RZ + D, slo + 2 * RZ + D, ring, sp, smc, regc);
     slo = slo + 1 == S ? 0 : slo + 1;
+}
+
+// Two planes per barrier (z and z+1): half the __syncthreads of vplane_fast.
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
+__device__ __forceinline__ void vplane_pair(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
+                                            T *ring, StepPtrs<T> &sp, T *smc,
+                                            VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
+    constexpr int RZ = SH::RZ;
+    constexpr int S = vec_slots<RZ, D>();
+    cp_async_wait<D - 2>();
+    __syncthreads();
+    const int slo1 = slo + 1 == S ? 0 : slo + 1;
+    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z, slo, last, ring, sp, smc, regc);
+    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z + 1, slo1, last, ring, sp, smc, regc);
+    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + RZ + D, slo + 2 * RZ + D, ring, sp, smc, regc);
+    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + 1 + RZ + D, slo + 2 * RZ + D + 1, ring, sp, smc, regc);
+    slo = slo1 + 1 == S ? 0 : slo1 + 1;
 }
 
 template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
 __device__ __forceinline__ void vsegment(const PersistentArgs &a, const VecPlan &tp, int z0, int z1, int &slo,
                                          bool last, T *ring, StepPtrs<T> &sp, T *smc,
                                          VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
-    for (int z = z0; z < z1; ++z)
-        vplane_fast<T, SH, V, ZR, D, PER_STEP, STORE, FILL>(a, tp, z, slo, last, ring, sp, smc, regc);
+    int z = z0;
+    for (; z + 1 < z1; z += 2)
+        vplane_pair<T, SH, V, ZR, D, PER_STEP, STORE, FILL>(a, tp, z, slo, last, ring, sp, smc, regc);
+    if (z < z1) vplane_fast<T, SH, V, ZR, D, PER_STEP, STORE, FILL>(a, tp, z, slo, last, ring, sp, smc, regc);
 }
 
 // One Jacobi step of one tile: fill the ring with planes -RZ.., then walk
@@ -544,7 +436,7 @@ template <typename T, class SH, int V, int ZR, int D, bool PER_STEP>
 __device__ __forceinline__ int vec_step(const PersistentArgs &a, const VecPlan &tp, long long k, bool last,
                                         int sb, T *ring, T *smc, VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     constexpr int RZ = SH::RZ;
-    constexpr int S = 2 * RZ + 1 + D;
+    constexpr int S = vec_slots<RZ, D>();
     constexpr int LEAD = RZ + D;  // fill distance ahead of the plane being computed
     const int src = (int)(k & 1);
     const T *fs = static_cast<const T *>(a.field[src]);
@@ -659,7 +551,7 @@ __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_c
     using VT = VecOf<T, V>;
     using PT = PairOf<T>;
     constexpr int RZ = SH::RZ;
-    constexpr int S = 2 * RZ + 1 + D;
+    constexpr int S = vec_slots<RZ, D>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *smc = ring + (long long)S * a.plane;
@@ -682,6 +574,21 @@ __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_c
         }
     }
     cp_async_wait_all();
+}
+
+// Registry entry of one instantiation of the vectorised kernel.
+template <typename T, class SH, int NT, int V, int ZR, int D, bool PS>
+KernelEntry vec_entry(int dtype, int shape) {
+    KernelEntry e;
+    e.dtype = dtype;
+    e.shape = shape;
+    e.per_step = PS;
+    e.fn = perks_stencil_vec_kernel<T, SH, NT, V, ZR, D, PS>;
+    e.nt = NT;
+    e.zr = ZR;
+    e.d = D;
+    e.v = V;
+    return e;
 }
 
 }  // namespace perks

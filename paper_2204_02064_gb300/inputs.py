@@ -187,3 +187,80 @@ def batch_domains(count: int = 64, seed: int = SEED_BATCH, lo: int = 128, hi: in
         out.append(dict(shape=(int(s), int(s)), name=name, offsets=shape_offsets(name), weights=w,
                         seed=substream(seed, 1000 + i)))
     return out
+
+
+# --------------------------------------------------------------------------
+# Variable-coefficient Poisson: Gaussian random fields
+# --------------------------------------------------------------------------
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """n standard normal doubles by Box-Muller from two SplitMix64 streams."""
+    u1 = uniform(substream(seed, 21), n)
+    u2 = uniform(substream(seed, 22), n)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def _grf_spectrum(n: int, ell: float, sigma: float):
+    """Square roots of the eigenvalues of the circulant embedding of the
+    squared-exponential covariance sigma^2 exp(-r^2 / (2 ell^2)) on an M x M
+    torus (M a power of two >= max(2n, n + 8 ell)), scaled by 1/M."""
+    m = 1
+    while m < max(2 * n, n + 8 * ell):
+        m *= 2
+    d = np.minimum(np.arange(m), m - np.arange(m)).astype(np.float64)
+    c = sigma ** 2 * np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2.0 * ell ** 2))
+    lam = np.maximum(np.fft.fft2(c).real, 0.0)
+    return np.sqrt(lam) / m, m
+
+
+def grf(n: int, count: int, seed: int, ell: float = 32.0, sigma: float = 1.0) -> np.ndarray:
+    """`count` n x n samples of a zero-mean stationary Gaussian field with
+    covariance sigma^2 exp(-r^2 / (2 ell^2)) (r in cells), by circulant
+    embedding (Dietrich & Newsam 1997): F(sqrt(lambda / M^2) xi) for complex
+    standard normal xi gives two independent fields (real and imaginary
+    parts); each is cropped to its top-left n x n block."""
+    sq, m = _grf_spectrum(n, ell, sigma)
+    out = np.empty((count, n, n))
+    for i in range((count + 1) // 2):
+        s = substream(seed, 1000 + i)
+        xi = normal(s, m * m).reshape(m, m) + 1j * normal(substream(s, 1), m * m).reshape(m, m)
+        z = np.fft.fft2(sq * xi)
+        out[2 * i] = z.real[:n, :n]
+        if 2 * i + 1 < count:
+            out[2 * i + 1] = z.imag[:n, :n]
+    return out
+
+
+def poisson_problems(n: int, count: int, seed: int = SEED_POISSON, ell: float = 32.0, sigma: float = 1.0):
+    """(k, f): k = exp(GRF), f uniform in [-1, 1); arrays (count, n, n)."""
+    k = np.exp(grf(n, count, substream(seed, 31), ell, sigma))
+    f = 2.0 * uniform(substream(seed, 32), count * n * n).reshape(count, n, n) - 1.0
+    return k, f
+
+
+def poisson_problems_device(n: int, count: int, seed: int = SEED_POISSON, ell: float = 32.0, sigma: float = 1.0,
+                            device: str = "cuda"):
+    """The same construction drawn on the device for large batches: torch's
+    seeded generator supplies the normals and uniforms, torch.fft the
+    transform (input synthesis only; different numbers from `poisson_problems`
+    with the same distribution)."""
+    import torch
+    sq, m = _grf_spectrum(n, ell, sigma)
+    sq_t = torch.from_numpy(sq).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    k = torch.empty((count, n, n), dtype=torch.float64, device=device)
+    chunk = 16
+    for i0 in range(0, (count + 1) // 2, chunk):
+        i1 = min((count + 1) // 2, i0 + chunk)
+        xi = torch.complex(torch.randn((i1 - i0, m, m), generator=g, dtype=torch.float64, device=device),
+                           torch.randn((i1 - i0, m, m), generator=g, dtype=torch.float64, device=device))
+        z = torch.fft.fft2(sq_t * xi)[:, :n, :n]
+        for j in range(i1 - i0):
+            a = 2 * (i0 + j)
+            k[a] = z[j].real
+            if a + 1 < count:
+                k[a + 1] = z[j].imag
+    k.exp_()
+    f = torch.rand((count, n, n), generator=g, dtype=torch.float64, device=device).mul_(2.0).sub_(1.0)
+    return k, f

@@ -1,0 +1,66 @@
+"""GPU parity of the batched variable-coefficient Poisson operator and its
+persistent CG against the oracle (CSR of the same finite-volume operator)."""
+import numpy as np
+import pytest
+
+from paper_2204_02064_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2204_02064_gb300 import api
+    return api.Context(0)
+
+
+def _k(nprob, ny, nx, seed):
+    return np.exp(2.0 * inputs.uniform(seed, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0)
+
+
+def test_apply_matches_oracle(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 3, 37, 53
+    k = _k(nprob, ny, nx, 1)
+    v = inputs.uniform(2, nprob * ny * nx).reshape(nprob, ny, nx) - 0.5
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    y = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    P.apply(torch.from_numpy(v).cuda(), y)
+    torch.cuda.synchronize()
+    for i in range(nprob):
+        rp, c, val = oracle.poisson_csr(k[i])
+        ref = oracle.spmv(rp, c, val, v[i].ravel())
+        assert np.max(np.abs(y[i].cpu().numpy().ravel() - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nprob,ny,nx", [(5, 24, 31), (300, 16, 16)])
+def test_batched_cg_matches_oracle(ctx, oracle, nprob, ny, nx):
+    """Every problem reaches the tolerance; iterations and solutions agree
+    with the oracle's CG on the CSR form of the same operator."""
+    from paper_2204_02064_gb300 import api
+    k = _k(nprob, ny, nx, 3)
+    f = 2.0 * inputs.uniform(4, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    res = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
+    xs = x.cpu().numpy()
+    assert res["max_true_rel_residual"] <= 1e-8
+    for i in range(0, nprob, max(1, nprob // 7)):
+        rp, c, val = oracle.poisson_csr(k[i])
+        ref = oracle.cg(rp, c, val, f[i].ravel(), rtol=1e-8, max_iter=20000)
+        assert abs(int(res["iterations"][i]) - ref["iters"]) <= 2
+        assert np.linalg.norm(xs[i].ravel() - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+
+
+def test_warm_start_with_exact_solution_needs_no_iteration(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 2, 20, 20
+    k = _k(nprob, ny, nx, 5)
+    u = inputs.uniform(6, nprob * ny * nx).reshape(nprob, ny, nx)
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    b = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    P.apply(torch.from_numpy(u).cuda(), b)
+    x = torch.from_numpy(u).cuda()
+    res = P.solve(b, x, rtol=1e-8)
+    assert res["max_iterations"] == 0

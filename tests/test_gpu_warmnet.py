@@ -1,0 +1,179 @@
+"""GPU parity of the warm-start network's kernels against the oracle, and
+the gain of the trained network as a CG warm start.
+
+Forward: F32 storage within 1e-4 of the fp64 oracle (relative to the output's
+max); BF16 storage against the oracle with every activation rounded to bf16
+as the kernels store it (1e-2: an fp32 sum that lands on a bf16 rounding
+boundary may round the other way).  Gradients: F32 storage within 1e-4 of
+the oracle's reverse-mode gradient (relative to the largest component); the
+oracle's gradient is itself pinned by central differences.
+"""
+import numpy as np
+import pytest
+
+from paper_2204_02064_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+C1 = 32
+DIL = (1, 2, 4, 8)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2204_02064_gb300 import api
+    return api.Context(0)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for co, ci in [(C1, 2), (C1, C1), (C1, C1), (1, C1)]:
+        parts += [rng.standard_normal(co * ci * 9) * scale * np.sqrt(2.0 / (9 * ci)),
+                  rng.standard_normal(co) * 0.05]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _case(nimg, ny, nx, seed):
+    k, f = inputs.poisson_problems(max(ny, nx), nimg, seed=seed, ell=4.0)
+    return k[:, :ny, :nx].copy(), f[:, :ny, :nx].copy()
+
+
+def _features(k, f, rnd=lambda a: a):
+    return np.stack([rnd(np.log(k)), rnd(f)], axis=1)
+
+
+@pytest.mark.parametrize("shape", [(2, 20, 23), (1, 16, 16), (3, 37, 5)])
+def test_forward_f32_matches_oracle(ctx, oracle, shape):
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = shape
+    k, f = _case(nimg, ny, nx, 41)
+    net = api.WarmNet(ctx, storage=api.F32, dilations=DIL, seed=1)
+    p = _params(3)
+    net.params = p
+    net.scale = 2.5
+    u = torch.zeros((nimg, ny, nx), dtype=torch.float64, device="cuda")
+    net.predict(_dev(k), _dev(f), u)
+    torch.cuda.synchronize()
+    x = _features(k, f, lambda a: a.astype(np.float32).astype(np.float64))
+    ref = np.stack([oracle.warmnet_forward(p.astype(np.float64), x[i], C1, DIL) for i in range(nimg)]) * 2.5
+    got = u.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_forward_bf16_matches_rounded_oracle(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = 2, 33, 40
+    k, f = _case(nimg, ny, nx, 42)
+    net = api.WarmNet(ctx, storage=api.BF16, dilations=DIL, seed=1)
+    p = _params(4)
+    net.params = p
+    net.scale = 1.0
+    u = torch.zeros((nimg, ny, nx), dtype=torch.float64, device="cuda")
+    net.predict(_dev(k), _dev(f), u)
+    torch.cuda.synchronize()
+    rb = oracle.bf16_round
+    x = _features(k, f, lambda a: rb(a.astype(np.float32)).astype(np.float64))
+    pd = p.astype(np.float64)
+    offs, o = [], 0
+    for co, ci in [(C1, 2), (C1, C1), (C1, C1), (1, C1)]:
+        W = pd[o:o + co * ci * 9].reshape(co, ci, 3, 3)
+        o += co * ci * 9
+        B = pd[o:o + co]
+        o += co
+        offs.append((W, B))
+    ref = []
+    for i in range(nimg):
+        y = x[i]
+        for l, (W, B) in enumerate(offs):
+            y = oracle.conv2d(y, W, B, DIL[l])
+            if l < 3:
+                y = rb(np.maximum(y, 0).astype(np.float32)).astype(np.float64)
+        ref.append(y[0])
+    ref = np.stack(ref)
+    got = u.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-2 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [(2, 20, 23), (3, 16, 33)])
+def test_gradient_f32_matches_oracle(ctx, oracle, shape):
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = shape
+    k, f = _case(nimg, ny, nx, 43)
+    u = inputs.uniform(44, nimg * ny * nx).reshape(nimg, ny, nx) * 3.0 - 1.0
+    net = api.WarmNet(ctx, storage=api.F32, dilations=DIL, seed=1)
+    p = _params(5)
+    net.params = p
+    net.scale = 1.5
+    loss, g = net.gradient(_dev(k), _dev(f), _dev(u))
+    x = _features(k, f, lambda a: a.astype(np.float32).astype(np.float64))
+    ref_loss, ref_g = oracle.warmnet_grad(p.astype(np.float64), x, u / 1.5, C1, DIL)
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
+
+
+def test_gradient_bf16_close_to_oracle(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = 2, 24, 24
+    k, f = _case(nimg, ny, nx, 45)
+    u = inputs.uniform(46, nimg * ny * nx).reshape(nimg, ny, nx) * 2.0 - 1.0
+    net = api.WarmNet(ctx, storage=api.BF16, dilations=DIL, seed=1)
+    p = _params(6)
+    net.params = p
+    loss, g = net.gradient(_dev(k), _dev(f), _dev(u))
+    x = _features(k, f)
+    ref_loss, ref_g = oracle.warmnet_grad(p.astype(np.float64), x, u, C1, DIL)
+    assert loss == pytest.approx(ref_loss, rel=5e-2)
+    assert np.linalg.norm(g - ref_g) <= 5e-2 * np.linalg.norm(ref_g)
+
+
+def test_adam_step_matches_formula(ctx):
+    """One Adam step from zero moments moves every parameter by
+    lr * g / (|g| + eps) (bias-corrected first step)."""
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = 1, 16, 16
+    k, f = _case(nimg, ny, nx, 47)
+    u = inputs.uniform(48, nimg * ny * nx).reshape(nimg, ny, nx)
+    net = api.WarmNet(ctx, storage=api.F32, dilations=DIL, seed=2)
+    p0 = net.params
+    _, g = net.gradient(_dev(k), _dev(f), _dev(u))
+    net.train_step(_dev(k), _dev(f), _dev(u), lr=1e-3)
+    p1 = net.params
+    expect = p0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    assert np.max(np.abs(p1 - expect)) <= 1e-6
+
+
+def _solve(ctx, k, f, x0=None, rtol=1e-8):
+    from paper_2204_02064_gb300 import api
+    P = api.Poisson(ctx, k)
+    x = torch.zeros_like(f) if x0 is None else x0.clone()
+    res = P.solve(f, x, rtol=rtol)
+    return x, res
+
+
+def test_trained_net_gains_over_zero_start(ctx):
+    """Train on solver-generated pairs, then solve held-out problems to 1e-8
+    from zero and from the network's prediction: both reach the tolerance
+    (CG decides), and the warm start needs fewer iterations."""
+    from paper_2204_02064_gb300 import api
+    n, ntrain, ntest = 64, 512, 64
+    k, f = inputs.poisson_problems_device(n, ntrain + ntest, seed=inputs.SEED_POISSON, ell=4.0)
+    u, res = _solve(ctx, k[:ntrain].contiguous(), f[:ntrain].contiguous(), rtol=1e-10)
+    assert res["max_true_rel_residual"] <= 1e-10
+    net = api.WarmNet(ctx, storage=api.BF16, dilations=DIL, seed=3)
+    losses = net.fit(k[:ntrain].contiguous(), f[:ntrain].contiguous(), u, batch=16, epochs=30, lr=2e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    kt, ft = k[ntrain:].contiguous(), f[ntrain:].contiguous()
+    _, zero = _solve(ctx, kt, ft)
+    u0 = torch.zeros_like(ft)
+    net.predict(kt, ft, u0)
+    _, warm = _solve(ctx, kt, ft, x0=u0)
+    assert zero["max_true_rel_residual"] <= 1e-8 and warm["max_true_rel_residual"] <= 1e-8
+    print("zero-start mean iterations %.1f, warm-start %.1f, losses %s"
+          % (zero["mean_iterations"], warm["mean_iterations"], losses[[0, -1]]))
+    assert warm["mean_iterations"] < zero["mean_iterations"]
