@@ -241,6 +241,115 @@ def cg_leg(api, torch, ctx, K):
     return out
 
 
+def batch_leg(api, torch, ctx, K):
+    """The batched workload: 64 uneven 2-D domains (sides 128..2048, 3x3 box
+    1/9 and 5x5 box seeded weights), fp32, 500 steps in one persistent launch
+    after the autotuner picked the plan; the per-domain per-step baseline
+    beside it."""
+    from paper_2204_02064_gb300 import inputs
+    doms = inputs.batch_domains()
+    b = api.Batch(ctx, doms, dtype="f32")
+    fields = [torch.from_numpy(inputs.stencil_field(d["shape"], d["seed"])).float().cuda() for d in doms]
+    cells = float(sum(d["shape"][0] * d["shape"][1] for d in doms))
+    t0 = time.perf_counter()
+    tuned = b.autotune(5)
+    tune_s = time.perf_counter() - t0
+    out = {"domains": len(doms), "cells": cells, "steps": 500, "autotune_s": tune_s,
+           "plan": {k: tuned.get(k) for k in ("granularity", "width_cap", "grid_blocks", "tiles")}}
+    stream = torch.cuda.current_stream()
+    for variant, name in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
+        times = []
+        for i in range(K + 1):
+            for j, f in enumerate(fields):
+                b.set_field(j, f)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(500, variant=variant)
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                times.append(e0.elapsed_time(e1))
+        ms = min(times)
+        out[name] = {"ms": ms, "gcells": cells * 500 / (ms * 1e-3) / 1e9}
+    b.close()
+    return out
+
+
+def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, batch=16, lr=1e-3):
+    """The variable-coefficient Poisson workload: 256 problems on 512^2
+    grids, k = exp(GRF, length 32, sigma 1), f uniform[-1,1), Dirichlet 0;
+    CG to 1e-8 from zero vs from the BF16 warm-start network (inference
+    included), the network trained on `ntrain` pairs generated by the same
+    batched CG."""
+    from paper_2204_02064_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    out = {"n": n, "problems": nprob, "rtol": 1e-8, "train_pairs": ntrain, "epochs": epochs, "batch": batch}
+    # training pairs, generated and solved in chunks of nprob problems
+    t0 = time.perf_counter()
+    ks, fs, us = [], [], []
+    chunk_iters = []
+    for c0 in range(0, ntrain, nprob):
+        m = min(nprob, ntrain - c0)
+        k, f = inputs.poisson_problems_device(n, m, seed=inputs.substream(inputs.SEED_POISSON, 500 + c0))
+        P = api.Poisson(ctx, k)
+        u = torch.zeros_like(f)
+        r = P.solve(f, u, rtol=1e-8)
+        chunk_iters.append(r["mean_iterations"])
+        P.close()
+        ks.append(k)
+        fs.append(f)
+        us.append(u)
+    k_tr, f_tr, u_tr = torch.cat(ks), torch.cat(fs), torch.cat(us)
+    del ks, fs, us
+    torch.cuda.synchronize()
+    out["generate_s"] = time.perf_counter() - t0
+    out["generate_mean_iterations"] = float(np.mean(chunk_iters))
+    net = api.WarmNet(ctx, storage=api.BF16, seed=7)
+    t0 = time.perf_counter()
+    losses = net.fit(k_tr, f_tr, u_tr, batch=batch, epochs=epochs, lr=lr)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    out["epoch_loss"] = [float(v) for v in losses]
+    out["scale"] = net.scale
+    del k_tr, f_tr, u_tr
+    torch.cuda.empty_cache()
+    # held-out evaluation problems
+    k, f = inputs.poisson_problems_device(n, nprob, seed=inputs.SEED_POISSON)
+    P = api.Poisson(ctx, k)
+    x = torch.zeros_like(f)
+    u0 = torch.zeros_like(f)
+    res = {}
+    for name in ("zero", "warm"):
+        times = []
+        for rep in range(2):
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            ei = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "warm":
+                net.predict(k, f, x)
+            ei.record(stream)
+            P.solve(f, x, rtol=1e-8, stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            times.append((e0.elapsed_time(e1), e0.elapsed_time(ei)))
+        x.zero_()
+        if name == "warm":
+            net.predict(k, f, x)
+        stats = P.solve(f, x, rtol=1e-8)
+        ms, ms_inf = min(times)
+        res[name] = {"ms_to_tol": ms, "inference_ms": ms_inf if name == "warm" else 0.0,
+                     "mean_iterations": stats["mean_iterations"], "max_iterations": stats["max_iterations"],
+                     "max_true_rel_residual": stats["max_true_rel_residual"]}
+    out.update(res)
+    out["speedup"] = res["zero"]["ms_to_tol"] / res["warm"]["ms_to_tol"]
+    P.close()
+    net.close()
+    return out
+
+
 def cpu_baseline_sample(max_seconds=15.0):
     """The oracle on a bounded sample of the workload: the 384^3 3d7pt field
     for as many whole steps as fit in ~max_seconds (at least one)."""
@@ -304,7 +413,19 @@ def main():
                     help="run one small case for ncu and exit: headline, stencil3d-f64, "
                          "stencil3d-f32, stencil3d-bf16, stencil3d-f64-perstep, "
                          "stencil3d-f32-perstep, cg-fp64, cg-fp32ir")
+    ap.add_argument("--leg", default=None, choices=["warmstart"],
+                    help="run one extra workload and print its JSON (warmstart: the learned "
+                         "warm start for the 512^2 x 256 Poisson problems)")
+    ap.add_argument("--ws-train", type=int, default=10000, help="warm start: training pairs")
+    ap.add_argument("--ws-epochs", type=int, default=4, help="warm start: training epochs")
     args = ap.parse_args()
+    if args.leg == "warmstart":
+        import torch
+        from paper_2204_02064_gb300 import api
+        ctx = api.Context(0)
+        print(json.dumps({"leg": "warmstart", **warmstart_leg(api, torch, ctx, ntrain=args.ws_train,
+                                                                epochs=args.ws_epochs)}), flush=True)
+        return 0
     if args.profile:
         return profile_case(args.profile)
     if args.warmup < 3:
@@ -409,6 +530,10 @@ def main():
             variants["cg"] = cg_leg(api, torch, ctx, 2)
         except Exception as e:
             variants["cg"] = {"error": str(e)}
+        try:
+            variants["batch64"] = batch_leg(api, torch, ctx, 2)
+        except Exception as e:
+            variants["batch64"] = {"error": str(e)}
 
     e2e_ms, h2d, d2h = e2e_leg(api, torch, ctx, L_3D, STEPS_3D, max(1, min(args.steps, 3)), 1)
     e2e_ms = _max_over_ranks(world, e2e_ms)
