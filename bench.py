@@ -276,15 +276,17 @@ def batch_leg(api, torch, ctx, K):
     return out
 
 
-def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, batch=16, lr=1e-3):
+def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, batch=16, lr=1e-3,
+                  label_rtol=1e-6, max_iter=100000):
     """The variable-coefficient Poisson workload: 256 problems on 512^2
     grids, k = exp(GRF, length 32, sigma 1), f uniform[-1,1), Dirichlet 0;
     CG to 1e-8 from zero vs from the BF16 warm-start network (inference
     included), the network trained on `ntrain` pairs generated by the same
-    batched CG."""
+    batched CG (labels solved to label_rtol)."""
     from paper_2204_02064_gb300 import inputs
     stream = torch.cuda.current_stream()
-    out = {"n": n, "problems": nprob, "rtol": 1e-8, "train_pairs": ntrain, "epochs": epochs, "batch": batch}
+    out = {"n": n, "problems": nprob, "rtol": 1e-8, "train_pairs": ntrain, "epochs": epochs, "batch": batch,
+           "label_rtol": label_rtol}
     # training pairs, generated and solved in chunks of nprob problems
     t0 = time.perf_counter()
     ks, fs, us = [], [], []
@@ -294,8 +296,10 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, bat
         k, f = inputs.poisson_problems_device(n, m, seed=inputs.substream(inputs.SEED_POISSON, 500 + c0))
         P = api.Poisson(ctx, k)
         u = torch.zeros_like(f)
-        r = P.solve(f, u, rtol=1e-8)
+        r = P.solve(f, u, rtol=label_rtol, max_iter=max_iter)
         chunk_iters.append(r["mean_iterations"])
+        print(f"warmstart: pairs {c0 + m}/{ntrain} solved, mean iterations {r['mean_iterations']:.0f}, "
+              f"{time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
         P.close()
         ks.append(k)
         fs.append(f)
@@ -321,25 +325,24 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, bat
     u0 = torch.zeros_like(f)
     res = {}
     for name in ("zero", "warm"):
-        times = []
-        for rep in range(2):
-            x.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            ei = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if name == "warm":
-                net.predict(k, f, x)
-            ei.record(stream)
-            P.solve(f, x, rtol=1e-8, stats=False)
-            e1.record(stream)
-            e1.synchronize()
-            times.append((e0.elapsed_time(e1), e0.elapsed_time(ei)))
+        x.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        ei = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if name == "warm":
+            net.predict(k, f, x)
+        ei.record(stream)
+        P.solve(f, x, rtol=1e-8, max_iter=max_iter, stats=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms, ms_inf = e0.elapsed_time(e1), e0.elapsed_time(ei)
+        # the same solve again for the per-problem statistics (untimed)
         x.zero_()
         if name == "warm":
             net.predict(k, f, x)
-        stats = P.solve(f, x, rtol=1e-8)
-        ms, ms_inf = min(times)
+        stats = P.solve(f, x, rtol=1e-8, max_iter=max_iter)
         res[name] = {"ms_to_tol": ms, "inference_ms": ms_inf if name == "warm" else 0.0,
                      "mean_iterations": stats["mean_iterations"], "max_iterations": stats["max_iterations"],
                      "max_true_rel_residual": stats["max_true_rel_residual"]}

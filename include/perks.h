@@ -117,7 +117,9 @@ typedef struct {
     int32_t smem_cache_planes;          /* -1: as many as fit; >= 0: at most this many */
     int32_t reg_cache;                  /* 0: no register cache; 1: the compiled register depth */
     int32_t reserved[4];                /* reserved[0] = 1: one-cell-per-thread kernel instead of
-                                           the 16-byte-vector kernel; others must be 0 */
+                                           the 16-byte-vector kernel; reserved[1] = planes per
+                                           block barrier of the vector kernel (2 or 4, 0 =
+                                           automatic); others must be 0 */
 } perks_stencil_plan;
 
 /* What a run did; filled by perks_stencil_run when asked. */
@@ -142,6 +144,17 @@ typedef struct {
 perks_status perks_stencil_create(perks_context *ctx, const perks_stencil_desc *desc,
                                   perks_stencil **out);
 perks_status perks_stencil_destroy(perks_stencil *st);
+
+/* Step trace of the persistent kernel (a tracing aid, not in the paper):
+ * with steps > 0 the next persistent runs record, for every block, the
+ * %globaltimer value (ns) when it starts and ends its work in each of the
+ * first `steps` time steps (and in the prologue, as step -1); steps = 0 turns
+ * tracing off.  get_trace copies 2 * (steps + 1) * grid_blocks values of the
+ * last traced run, laid out [step + 1][block][start, end], into `host`.
+ * Errors: INVALID_ARG (no traced run, capacity too small), OUT_OF_MEMORY. */
+perks_status perks_stencil_set_trace(perks_stencil *st, int32_t steps);
+perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t capacity,
+                                     int32_t *grid_blocks, int32_t *steps);
 
 /* Plan override (NULL resets to automatic).  Errors: INVALID_ARG,
  * UNSUPPORTED (the persistent kernel cannot host the requested tiles). */

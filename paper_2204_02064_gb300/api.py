@@ -125,6 +125,8 @@ def _declare(lib):
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_op_set_spmv": ([P, i32], i32),
+        "perks_stencil_set_trace": ([P, i32], i32),
+        "perks_stencil_get_trace": ([P, P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "perks_poisson_create": ([P, i32, i32, i32, P, ctypes.c_int, ctypes.POINTER(P)], i32),
         "perks_poisson_destroy": ([P], i32),
         "perks_poisson_apply": ([P, P, P, P], i32),
@@ -318,15 +320,37 @@ class Stencil:
         self.cells = int(np.prod(shape))
 
     def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1,
-                 scalar: bool = False):
+                 scalar: bool = False, planes_per_barrier: int = 0):
         """Plan override; ``scalar`` selects the one-cell-per-thread kernel
-        instead of the 16-byte-vector kernel."""
+        instead of the 16-byte-vector kernel; ``planes_per_barrier`` (2 or 4,
+        0 = automatic) picks how many planes the vector kernel computes
+        between two block barriers."""
         p = StencilPlan()
         p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
         p.smem_cache_planes = int(smem_cache_planes)
         p.reg_cache = int(reg_cache)
         p.reserved[0] = 1 if scalar else 0
+        p.reserved[1] = int(planes_per_barrier)
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
+
+    def set_trace(self, steps: int):
+        """Record per-block start/end times of the first ``steps`` steps of the
+        next persistent runs (0 turns tracing off)."""
+        self.ctx.check(self._lib.perks_stencil_set_trace(self.handle, int(steps)))
+        self._trace_steps = int(steps)
+
+    def trace(self) -> np.ndarray:
+        """(steps + 1, blocks, 2) array of %globaltimer ns of the last traced
+        run: [k + 1, block] = (start, end) of the block's work in step k
+        (k = -1: prologue)."""
+        steps = getattr(self, "_trace_steps", 0)
+        cap = 2 * (steps + 1) * 4 * 1024
+        buf = np.zeros(cap, dtype=np.uint64)
+        g = ctypes.c_int32()
+        n = ctypes.c_int32()
+        self.ctx.check(self._lib.perks_stencil_get_trace(self.handle, buf.ctypes.data, cap, ctypes.byref(g),
+                                                         ctypes.byref(n)))
+        return buf[:2 * (n.value + 1) * g.value].reshape(n.value + 1, g.value, 2)
 
     def reset_plan(self):
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, None))

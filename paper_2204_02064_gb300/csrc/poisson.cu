@@ -20,7 +20,7 @@ using namespace perks;
 
 namespace {
 
-constexpr int kPoiThreads = 512;
+constexpr int kPoiThreads = 256;
 
 struct PoissonArgs {
     int nx, ny, nprob;
@@ -88,11 +88,45 @@ __device__ __forceinline__ double apply_cell(const double *__restrict__ fxp, con
     return acc;
 }
 
-// Visits every cell of one problem, rows outer, threads across a row.
-#define FOR_CELLS(nx, ny, i, j, c)                                  \
-    for (int j = 0; j < (ny); ++j)                                  \
-        for (int i = threadIdx.x; i < (nx); i += blockDim.x)        \
-            if (const long long c = (long long)j * (nx) + i; true)
+// (A v) for kRows consecutive cells (i, j0..j0+kRows-1) of one column, with
+// each value loaded once (v down the column, faces once per row) and the same
+// arithmetic, in the same order, as apply_cell.  Rows at or beyond ny are
+// skipped.
+template <int K>
+__device__ __forceinline__ void apply_column(const double *__restrict__ fxp, const double *__restrict__ fyp,
+                                             const double *__restrict__ v, int nx, int ny, int i, int j0,
+                                             double (&out)[K], double (&vc)[K]) {
+    double col[K + 2];
+    double fyv[K + 1];
+#pragma unroll
+    for (int u = -1; u <= K; ++u) {
+        const int j = j0 + u;
+        col[u + 1] = (j >= 0 && j < ny) ? v[(long long)j * nx + i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u <= K; ++u) {
+        const int j = j0 + u;
+        fyv[u] = (j <= ny) ? __ldg(fyp + (long long)j * nx + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const int j = j0 + u;
+        if (j < ny) {
+            const long long c = (long long)j * nx + i;
+            const double *fr = fxp + (long long)j * (nx + 1) + i;
+            const double fw = __ldg(fr), fe = __ldg(fr + 1);
+            const double fs = fyv[u], fn = fyv[u + 1];
+            const double vcen = col[u + 1];
+            double acc = ((fw + fe) + (fs + fn)) * vcen;
+            if (i > 0) acc = fma(-fw, v[c - 1], acc);
+            if (i + 1 < nx) acc = fma(-fe, v[c + 1], acc);
+            if (j > 0) acc = fma(-fs, col[u], acc);
+            if (j + 1 < ny) acc = fma(-fn, col[u + 2], acc);
+            out[u] = acc;
+            vc[u] = vcen;
+        }
+    }
+}
 
 __device__ __forceinline__ double bsum(double v, double *red) {
     v = warp_sum(v);
@@ -110,6 +144,49 @@ __device__ __forceinline__ double bsum(double v, double *red) {
     return red[32];
 }
 
+// Row-blocked traversal: each thread takes cell column i of kRows rows at a
+// time, so the loads of kRows independent cells (and their neighbours) are in
+// flight together instead of one row's worth per memory round trip.
+constexpr int kRows = 4;
+// Linear traversal unroll for the vector updates.
+constexpr int kLin = 2;
+
+// r = b - A x over the whole problem; returns this thread's partial <r,r>
+// (and <b,b> through bb); optionally p = r.
+template <bool SET_P>
+__device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, const double *__restrict__ fyp,
+                                                const double *__restrict__ b, const double *__restrict__ x,
+                                                double *__restrict__ r, double *__restrict__ p, int nx, int ny,
+                                                double &bb) {
+    double rr = 0.0;
+    for (int j0 = 0; j0 < ny; j0 += kRows)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            double rv[kRows], bv[kRows], xc[kRows];
+            apply_column<kRows>(fxp, fyp, x, nx, ny, i, j0, rv, xc);
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int j = j0 + u;
+                if (j < ny) {
+                    const long long c = (long long)j * nx + i;
+                    bv[u] = __ldg(b + c);
+                    rv[u] = bv[u] - rv[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int j = j0 + u;
+                if (j < ny) {
+                    const long long c = (long long)j * nx + i;
+                    r[c] = rv[u];
+                    if (SET_P) p[c] = rv[u];
+                    bb = fma(bv[u], bv[u], bb);
+                    rr = fma(rv[u], rv[u], rr);
+                }
+            }
+        }
+    return rr;
+}
+
 __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const __grid_constant__ PoissonArgs a) {
     __shared__ double red[33];
     __shared__ int s_prob;
@@ -121,19 +198,16 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
         const int pb = s_prob;
         __syncthreads();
         if (pb >= a.nprob) break;
-        const double *fxp = a.fx + (long long)pb * (nx + 1) * ny;
-        const double *fyp = a.fy + (long long)pb * nx * (ny + 1);
-        const double *b = a.b + pb * n;
-        double *x = a.x + pb * n, *r = a.r + pb * n, *p = a.p + pb * n, *q = a.q + pb * n;
+        const double *__restrict__ fxp = a.fx + (long long)pb * (nx + 1) * ny;
+        const double *__restrict__ fyp = a.fy + (long long)pb * nx * (ny + 1);
+        const double *__restrict__ b = a.b + pb * n;
+        double *__restrict__ x = a.x + pb * n;
+        double *__restrict__ r = a.r + pb * n;
+        double *__restrict__ p = a.p + pb * n;
+        double *__restrict__ q = a.q + pb * n;
         // r = b - A x, p = r
-        double bb = 0.0, rr = 0.0;
-        FOR_CELLS(nx, ny, i, j, c) {
-            const double ri = b[c] - apply_cell(fxp, fyp, x, nx, ny, i, j);
-            r[c] = ri;
-            p[c] = ri;
-            bb = fma(b[c], b[c], bb);
-            rr = fma(ri, ri, rr);
-        }
+        double bb = 0.0;
+        double rr = residual_pass<true>(fxp, fyp, b, x, r, p, nx, ny, bb);
         bb = bsum(bb, red);
         rr = bsum(rr, red);
         const double tol2 = a.rtol * a.rtol * bb;
@@ -142,42 +216,70 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
             if (rr <= tol2) { status = PERKS_OK; break; }
             bool converged = false;
             while (it < a.max_iter) {
+                // q = A p, <p, q>
                 double pq = 0.0;
-                FOR_CELLS(nx, ny, i, j, c) {
-                    const double qc = apply_cell(fxp, fyp, p, nx, ny, i, j);
-                    q[c] = qc;
-                    pq = fma(p[c], qc, pq);
-                }
+                for (int j0 = 0; j0 < ny; j0 += kRows)
+                    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                        double qv[kRows], pv[kRows];
+                        apply_column<kRows>(fxp, fyp, p, nx, ny, i, j0, qv, pv);
+#pragma unroll
+                        for (int u = 0; u < kRows; ++u) {
+                            const int j = j0 + u;
+                            if (j < ny) {
+                                q[(long long)j * nx + i] = qv[u];
+                                pq = fma(pv[u], qv[u], pq);
+                            }
+                        }
+                    }
                 pq = bsum(pq, red);
                 if (!(pq > 0.0) || !isfinite(pq)) { status = PERKS_ERR_BREAKDOWN; break; }
                 const double alpha = rr / pq;
+                // x += alpha p, r -= alpha q, <r, r>
                 double rn = 0.0;
-                for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-                    x[c] = fma(alpha, p[c], x[c]);
-                    const double ri = fma(-alpha, q[c], r[c]);
-                    r[c] = ri;
-                    rn = fma(ri, ri, rn);
+                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * kLin) {
+                    double xv[kLin], rv[kLin], pv[kLin], qv[kLin];
+#pragma unroll
+                    for (int u = 0; u < kLin; ++u) {
+                        const long long c = c0 + (long long)u * blockDim.x;
+                        if (c < n) { xv[u] = x[c]; rv[u] = r[c]; pv[u] = p[c]; qv[u] = q[c]; }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLin; ++u) {
+                        const long long c = c0 + (long long)u * blockDim.x;
+                        if (c < n) {
+                            x[c] = fma(alpha, pv[u], xv[u]);
+                            const double ri = fma(-alpha, qv[u], rv[u]);
+                            r[c] = ri;
+                            rn = fma(ri, ri, rn);
+                        }
+                    }
                 }
                 rn = bsum(rn, red);
                 const double beta = rn / rr;
-                for (long long c = threadIdx.x; c < n; c += blockDim.x) p[c] = fma(beta, p[c], r[c]);
+                // p = r + beta p
+                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * kLin) {
+                    double rv[kLin], pv[kLin];
+#pragma unroll
+                    for (int u = 0; u < kLin; ++u) {
+                        const long long c = c0 + (long long)u * blockDim.x;
+                        if (c < n) { rv[u] = r[c]; pv[u] = p[c]; }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLin; ++u) {
+                        const long long c = c0 + (long long)u * blockDim.x;
+                        if (c < n) p[c] = fma(beta, pv[u], rv[u]);
+                    }
+                }
                 __syncthreads();
                 rr = rn;
                 ++it;
                 if (rr <= tol2) { converged = true; break; }
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
-            double tr = 0.0;
-            FOR_CELLS(nx, ny, i, j, c) {
-                const double ri = b[c] - apply_cell(fxp, fyp, x, nx, ny, i, j);
-                r[c] = ri;
-                tr = fma(ri, ri, tr);
-            }
-            rr = bsum(tr, red);
+            double bdum = 0.0;
+            rr = bsum(residual_pass<true>(fxp, fyp, b, x, r, p, nx, ny, bdum), red);
             if (rr <= tol2) { status = PERKS_OK; break; }
             if (!converged || restart >= a.max_restarts) break;
-            for (long long c = threadIdx.x; c < n; c += blockDim.x) p[c] = r[c];
-            __syncthreads();
         }
         if (threadIdx.x == 0) {
             a.iters[pb] = it;

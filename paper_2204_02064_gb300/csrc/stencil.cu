@@ -103,16 +103,22 @@ std::vector<KernelEntry> &registry() {
     return table;
 }
 
+// Planes per block barrier preferred by default where both variants exist.
+constexpr int kDefaultPlanesPerBarrier = 2;
+
 // Picks a kernel: the vectorised one when the x extent allows 16-byte
 // vectors (unless the plan asks for the scalar kernel), the scalar one
 // otherwise; with or without the register cache as requested.
-KernelEntry *find_kernel(int dtype, int shape, bool want_reg, bool per_step, int X, bool allow_vec) {
+KernelEntry *find_kernel(int dtype, int shape, bool want_reg, bool per_step, int X, bool allow_vec,
+                         int want_p = 0) {
     KernelEntry *best = nullptr;
+    const int pref_p = want_p > 0 ? want_p : kDefaultPlanesPerBarrier;
     for (KernelEntry &e : registry()) {
         if (e.dtype != dtype || e.shape != shape || e.per_step != per_step) continue;
         if (e.v > 1 && (!allow_vec || X % e.v != 0)) continue;
+        if (want_p > 0 && e.v > 1 && e.p != want_p) continue;
         auto score = [&](const KernelEntry &k) {
-            return (k.v > 1 ? 4 : 0) + ((k.zr > 0) == want_reg ? 2 : 0);
+            return (k.v > 1 ? 4 : 0) + ((k.zr > 0) == want_reg ? 2 : 0) + (k.p == pref_p ? 1 : 0);
         };
         if (!best || score(e) > score(*best)) best = &e;
     }
@@ -150,6 +156,8 @@ struct perks_stencil {
     double kw[kMaxKernelPoints] = {};
     bool has_plan = false;
     perks_stencil_plan plan{};
+    unsigned long long *trace = nullptr;  // optional step trace of the persistent kernel
+    int trace_steps = 0, trace_blocks = 0, trace_grid = 0;
 };
 
 namespace {
@@ -188,11 +196,15 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
                     "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt)");
     const ShapeInfo &sh = shape_by_id(st->shape_id);
     bool want_reg = true, allow_vec = true;
+    int want_p = 0;
     if (st->has_plan) {
         want_reg = st->plan.reg_cache != 0;
         allow_vec = st->plan.reserved[0] == 0;  // reserved[0] = 1 forces the scalar kernel
+        want_p = st->plan.reserved[1];          // planes per barrier (0 = automatic)
     }
-    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec);
+    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec, want_p);
+    if (!kp && want_p > 0)
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec, 0);
     if (!kp)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "no %s kernel for this dtype/shape/extent (bf16 needs nx divisible by 8)",
@@ -209,7 +221,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     }
     const int R = sh.radius;
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
-    const int S = 2 * RZ + 1 + k.d + (k.v > 1 ? 1 : 0);  // the vector kernel pairs planes (one more slot)
+    const int S = k.v > 1 ? 2 * RZ + k.p + k.d : 2 * RZ + 1 + k.d;  // ring slots (vector kernel: P planes per barrier)
     const int es = st->es;
     const int V = k.v;
     const int HX = V > 1 ? std::max(V, 2) : RX;  // ring pad columns on each side
@@ -397,6 +409,13 @@ perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, 
     a.bar = st->bar;
     a.err = st->err;
     a.timeout_ns = ctx->timeout_ns;
+    if (st->trace && pl.blocks <= st->trace_blocks) {
+        a.trace = st->trace;
+        a.trace_steps = st->trace_steps;
+        st->trace_grid = pl.blocks;
+        PERKS_CUDA(ctx, cudaMemsetAsync(st->trace, 0, sizeof(unsigned long long) * 2 * (size_t)(st->trace_steps + 1) *
+                                                          st->trace_blocks, s));
+    }
     PERKS_CUDA(ctx, cudaMemsetAsync(st->bar, 0, sizeof(unsigned long long), s));
     PERKS_CUDA(ctx, cudaMemsetAsync(st->err, 0, sizeof(DevError), s));
     void *args[] = {&a};
@@ -517,7 +536,37 @@ extern "C" perks_status perks_stencil_destroy(perks_stencil *st) {
     }
     if (st->bar) cudaFree(st->bar);
     if (st->err) cudaFree(st->err);
+    if (st->trace) cudaFree(st->trace);
     delete st;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_set_trace(perks_stencil *st, int32_t steps) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    if (steps < 0) return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_trace: steps < 0");
+    perks_status rc = use_device(st->ctx);
+    if (rc) return rc;
+    if (st->trace) cudaFree(st->trace);
+    st->trace = nullptr;
+    st->trace_steps = st->trace_blocks = st->trace_grid = 0;
+    if (steps == 0) return PERKS_OK;
+    const int blocks = 4 * st->ctx->sm_count;  // upper bound of any persistent grid
+    PERKS_CUDA(st->ctx, cudaMalloc(&st->trace, sizeof(unsigned long long) * 2 * (size_t)(steps + 1) * blocks));
+    st->trace_steps = steps;
+    st->trace_blocks = blocks;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t capacity,
+                                                int32_t *grid_blocks, int32_t *steps) {
+    if (!st || !host || !grid_blocks || !steps) return PERKS_ERR_INVALID_ARG;
+    if (!st->trace || st->trace_grid == 0)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_get_trace: no traced persistent run");
+    const long long need = 2LL * (st->trace_steps + 1) * st->trace_grid;
+    if (capacity < need) return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_get_trace: need %lld entries", need);
+    PERKS_CUDA(st->ctx, cudaMemcpy(host, st->trace, sizeof(uint64_t) * need, cudaMemcpyDeviceToHost));
+    *grid_blocks = st->trace_grid;
+    *steps = st->trace_steps;
     return PERKS_OK;
 }
 
@@ -526,6 +575,10 @@ extern "C" perks_status perks_stencil_set_plan(perks_stencil *st, const perks_st
     if (!plan) { st->has_plan = false; return PERKS_OK; }
     if (plan->tiles_x < 0 || plan->tiles_y < 0 || plan->tiles_z < 0 || plan->smem_cache_planes < -1)
         return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: negative field");
+    if (plan->reserved[1] != 0 && plan->reserved[1] != 2 && plan->reserved[1] != 4)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: planes per barrier must be 0, 2 or 4");
+    if (plan->reserved[2] != 0 || plan->reserved[3] != 0)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: reserved fields must be 0");
     st->plan = *plan;
     st->has_plan = true;
     return PERKS_OK;

@@ -84,7 +84,20 @@ struct PersistentArgs {
     unsigned long long *bar;
     DevError *err;
     long long timeout_ns;
+    // optional step trace (nullptr = off): %globaltimer of every block at the
+    // start and end of its work in step k (k = -1: the prologue), at
+    // trace[((k + 1) * gridDim.x + block) * 2 + {0, 1}], for k < trace_steps
+    unsigned long long *trace;
+    int trace_steps;
 };
+
+__device__ __forceinline__ void trace_mark(const PersistentArgs &a, long long k, int which) {
+    if (a.trace != nullptr && threadIdx.x == 0 && k < a.trace_steps) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.trace[((k + 1) * gridDim.x + blockIdx.x) * 2 + which] = t;
+    }
+}
 
 __host__ __device__ inline void split_axis(int n, int parts, int i, int &start, int &len) {
     const int base = n / parts, rem = n % parts;

@@ -28,6 +28,7 @@ struct KernelEntry {
     PersistentFn fn = nullptr;
     int nt = 0, zr = 0, d = 0;
     int v = 1;              // cells per thread along x (1: scalar kernel)
+    int p = 2;              // planes per block barrier (vectorised kernel)
     bool configured = false;
     int smem_budget = 0;    // dynamic shared memory available per block
 };

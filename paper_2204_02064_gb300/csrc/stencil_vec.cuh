@@ -231,9 +231,9 @@ __device__ __forceinline__ void load_cells(const T *p, T (&out)[N > 0 ? N : 1]) 
     }
 }
 
-// Ring slots of the vectorised kernel: planes z-RZ..z+1+RZ are read by a
-// paired iteration while two more are filled, D planes ahead.
-template <int RZ, int D> __host__ __device__ constexpr int vec_slots() { return 2 * RZ + 2 + D; }
+// Ring slots of the vectorised kernel: an iteration over P planes reads
+// planes z-RZ..z+P-1+RZ while P more are filled, D planes ahead.
+template <int RZ, int D, int P = 2> __host__ __device__ constexpr int vec_slots() { return 2 * RZ + P + D; }
 
 // Where a plane's own-column values come from (fill) or go to (store).
 enum PlaneClass : int { PC_REG = 0, PC_SMEM = 1, PC_GLOBAL = 2, PC_HALO = 3, PC_NONE = 4 };
@@ -290,7 +290,7 @@ __device__ __forceinline__ void vfill_fast(const PersistentArgs &a, const VecPla
 }
 
 // Computes plane z (ring slot of plane z-RZ = slo) and stores it.
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE>
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int P>
 __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const VecPlan &tp, int z, int slo, bool last,
                                                const T *ring, StepPtrs<T> &sp, T *smc,
                                                VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
@@ -300,7 +300,7 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
     using RW = RowsOf<SH>;
     constexpr int RZ = SH::RZ;
     constexpr int R = SH::R;
-    constexpr int S = vec_slots<RZ, D>();
+    constexpr int S = vec_slots<RZ, D, P>();
     constexpr int NR = RW::count();
     if (tp.own) {
         A seg[NR][V + 2 * R];
@@ -373,11 +373,11 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
 }
 
 // Starts the copy of plane q (= z + RZ + D) into its slot; one cp.async group.
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int FILL>
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int FILL, int P>
 __device__ __forceinline__ void vfill_next(const PersistentArgs &a, const VecPlan &tp, int q, int slo_q, T *ring,
                                            StepPtrs<T> &sp, const T *smc,
                                            const VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
-    constexpr int S = vec_slots<SH::RZ, D>();
+    constexpr int S = vec_slots<SH::RZ, D, P>();
     int s = slo_q;
     s = s >= S ? s - S : s;
     vfill_fast<T, SH, V, ZR, PER_STEP, FILL>(a, tp, q, ring + s * a.plane, sp, smc, regc);
@@ -387,56 +387,69 @@ __device__ __forceinline__ void vfill_next(const PersistentArgs &a, const VecPla
     cp_async_commit();
 }
 
-// One plane per barrier.
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
+// One plane per barrier (the remainder of a segment).
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL, int P>
 __device__ __forceinline__ void vplane_fast(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
                                             T *ring, StepPtrs<T> &sp, T *smc,
                                             VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     constexpr int RZ = SH::RZ;
-    constexpr int S = vec_slots<RZ, D>();
+    constexpr int S = vec_slots<RZ, D, P>();
     cp_async_wait<D - 1>();
     __syncthreads();
-    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z, slo, last, ring, sp, smc, regc);
-    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + RZ + D, slo + 2 * RZ + D, ring, sp, smc, regc);
+    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL, P>(a, tp, z + RZ + D, slo + 2 * RZ + D, ring, sp, smc, regc);
     slo = slo + 1 == S ? 0 : slo + 1;
 }
 
-// Two planes per barrier (z and z+1): half the __syncthreads of vplane_fast.
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
-__device__ __forceinline__ void vplane_pair(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
-                                            T *ring, StepPtrs<T> &sp, T *smc,
-                                            VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
+// P planes per barrier (z .. z+P-1): the block synchronises once per P
+// planes and every thread has P independent planes of loads and FMAs in
+// flight between two barriers.  Slot safety: the iteration reads ring slots
+// slo .. slo+2RZ+P-1 and fills slots slo+2RZ+D .. slo+2RZ+D+P-1; both ranges
+// lie within one turn of the S = 2RZ+P+D slots, so they never overlap, and
+// after wait_group<D-P> every plane up to z+P-1+RZ has landed.
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL, int P>
+__device__ __forceinline__ void vplane_multi(const PersistentArgs &a, const VecPlan &tp, int z, int &slo, bool last,
+                                             T *ring, StepPtrs<T> &sp, T *smc,
+                                             VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     constexpr int RZ = SH::RZ;
-    constexpr int S = vec_slots<RZ, D>();
-    cp_async_wait<D - 2>();
+    constexpr int S = vec_slots<RZ, D, P>();
+    static_assert(P >= 1 && P <= D, "planes per barrier");
+    cp_async_wait<D - P>();
     __syncthreads();
-    const int slo1 = slo + 1 == S ? 0 : slo + 1;
-    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z, slo, last, ring, sp, smc, regc);
-    vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE>(a, tp, z + 1, slo1, last, ring, sp, smc, regc);
-    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + RZ + D, slo + 2 * RZ + D, ring, sp, smc, regc);
-    vfill_next<T, SH, V, ZR, D, PER_STEP, FILL>(a, tp, z + 1 + RZ + D, slo + 2 * RZ + D + 1, ring, sp, smc, regc);
-    slo = slo1 + 1 == S ? 0 : slo1 + 1;
+    static_for<0, P>([&](auto PI) {
+        constexpr int p = decltype(PI)::value;
+        int s = slo + p;
+        s = s >= S ? s - S : s;
+        vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE, P>(a, tp, z + p, s, last, ring, sp, smc, regc);
+    });
+    static_for<0, P>([&](auto PI) {
+        constexpr int p = decltype(PI)::value;
+        vfill_next<T, SH, V, ZR, D, PER_STEP, FILL, P>(a, tp, z + p + RZ + D, slo + 2 * RZ + D + p, ring, sp, smc,
+                                                      regc);
+    });
+    slo = slo + P >= S ? slo + P - S : slo + P;
 }
 
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL>
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int STORE, int FILL, int P>
 __device__ __forceinline__ void vsegment(const PersistentArgs &a, const VecPlan &tp, int z0, int z1, int &slo,
                                          bool last, T *ring, StepPtrs<T> &sp, T *smc,
                                          VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     int z = z0;
-    for (; z + 1 < z1; z += 2)
-        vplane_pair<T, SH, V, ZR, D, PER_STEP, STORE, FILL>(a, tp, z, slo, last, ring, sp, smc, regc);
-    if (z < z1) vplane_fast<T, SH, V, ZR, D, PER_STEP, STORE, FILL>(a, tp, z, slo, last, ring, sp, smc, regc);
+    for (; z + P <= z1; z += P)
+        vplane_multi<T, SH, V, ZR, D, PER_STEP, STORE, FILL, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+    for (; z < z1; ++z)
+        vplane_fast<T, SH, V, ZR, D, PER_STEP, STORE, FILL, P>(a, tp, z, slo, last, ring, sp, smc, regc);
 }
 
 // One Jacobi step of one tile: fill the ring with planes -RZ.., then walk
 // the tile's planes in segments where both the store class of plane z and
 // the fill class of plane z+RZ+D are fixed.  `sb` is the ring slot of plane
 // -RZ; returns the slot for the next step.
-template <typename T, class SH, int V, int ZR, int D, bool PER_STEP>
+template <typename T, class SH, int V, int ZR, int D, bool PER_STEP, int P = 2>
 __device__ __forceinline__ int vec_step(const PersistentArgs &a, const VecPlan &tp, long long k, bool last,
                                         int sb, T *ring, T *smc, VecOf<T, V> (&regc)[ZR > 0 ? ZR : 1]) {
     constexpr int RZ = SH::RZ;
-    constexpr int S = vec_slots<RZ, D>();
+    constexpr int S = vec_slots<RZ, D, P>();
     constexpr int LEAD = RZ + D;  // fill distance ahead of the plane being computed
     const int src = (int)(k & 1);
     const T *fs = static_cast<const T *>(a.field[src]);
@@ -481,11 +494,11 @@ __device__ __forceinline__ int vec_step(const PersistentArgs &a, const VecPlan &
         for (int z = 0; z < ZR; ++z) {
             if (z < tz) {
                 const int q = z + LEAD;
-                if (q >= tz + RZ) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_NONE>(a, tp, z, slo, last, ring, sp, smc, regc);
-                else if (q >= tz) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_HALO>(a, tp, z, slo, last, ring, sp, smc, regc);
-                else if (q < ZR) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_REG>(a, tp, z, slo, last, ring, sp, smc, regc);
-                else if (q < zc) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_SMEM>(a, tp, z, slo, last, ring, sp, smc, regc);
-                else vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_GLOBAL>(a, tp, z, slo, last, ring, sp, smc, regc);
+                if (q >= tz + RZ) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_NONE, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+                else if (q >= tz) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_HALO, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+                else if (q < ZR) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_REG, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+                else if (q < zc) vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_SMEM, P>(a, tp, z, slo, last, ring, sp, smc, regc);
+                else vplane_fast<T, SH, V, ZR, D, PER_STEP, PC_REG, PC_GLOBAL, P>(a, tp, z, slo, last, ring, sp, smc, regc);
             }
         }
     }
@@ -501,11 +514,11 @@ __device__ __forceinline__ int vec_step(const PersistentArgs &a, const VecPlan &
         const int e1 = min(z1, max(z0, b_sg));
         const int e2 = min(z1, max(z0, b_gh));
         const int e3 = min(z1, max(z0, b_hn));
-        if (!PER_STEP) vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_SMEM>(a, tp, z0, e1, slo, last, ring, sp, smc, regc);
-        else vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_GLOBAL>(a, tp, z0, e1, slo, last, ring, sp, smc, regc);
-        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_GLOBAL>(a, tp, max(z0, e1), e2, slo, last, ring, sp, smc, regc);
-        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_HALO>(a, tp, max(z0, e2), e3, slo, last, ring, sp, smc, regc);
-        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_NONE>(a, tp, max(z0, e3), z1, slo, last, ring, sp, smc, regc);
+        if (!PER_STEP) vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_SMEM, P>(a, tp, z0, e1, slo, last, ring, sp, smc, regc);
+        else vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_GLOBAL, P>(a, tp, z0, e1, slo, last, ring, sp, smc, regc);
+        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_GLOBAL, P>(a, tp, max(z0, e1), e2, slo, last, ring, sp, smc, regc);
+        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_HALO, P>(a, tp, max(z0, e2), e3, slo, last, ring, sp, smc, regc);
+        vsegment<T, SH, V, ZR, D, PER_STEP, STORE, PC_NONE, P>(a, tp, max(z0, e3), z1, slo, last, ring, sp, smc, regc);
     };
     if (!PER_STEP) run(zr0, max(zr0, zc), std::integral_constant<int, PC_SMEM>{});
     run(max(zr0, zc), tz, std::integral_constant<int, PC_GLOBAL>{});
@@ -546,12 +559,12 @@ __device__ __forceinline__ void vec_prologue(const PersistentArgs &a, const VecP
     }
 }
 
-template <typename T, class SH, int NT, int V, int ZR, int D, bool PER_STEP>
+template <typename T, class SH, int NT, int V, int ZR, int D, bool PER_STEP, int P>
 __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_constant__ PersistentArgs a) {
     using VT = VecOf<T, V>;
     using PT = PairOf<T>;
     constexpr int RZ = SH::RZ;
-    constexpr int S = vec_slots<RZ, D>();
+    constexpr int S = vec_slots<RZ, D, P>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *smc = ring + (long long)S * a.plane;
@@ -561,14 +574,18 @@ __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_c
     unsigned long long epoch = 0;
 
     if (!PER_STEP) {
+        trace_mark(a, -1, 0);
         vec_prologue<T, SH, V, ZR>(a, tp, smc, regc);
+        trace_mark(a, -1, 1);
         if (!grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns)) return;
     }
 
     int sb = 0;
     for (long long k = 0; k < a.steps; ++k) {
         const bool last = (k + 1 == a.steps);
-        sb = vec_step<T, SH, V, ZR, D, PER_STEP>(a, tp, k, last, sb, ring, smc, regc);
+        if (!PER_STEP) trace_mark(a, k, 0);
+        sb = vec_step<T, SH, V, ZR, D, PER_STEP, P>(a, tp, k, last, sb, ring, smc, regc);
+        if (!PER_STEP) trace_mark(a, k, 1);
         if (!last) {
             if (!grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns)) break;
         }
@@ -577,17 +594,18 @@ __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_c
 }
 
 // Registry entry of one instantiation of the vectorised kernel.
-template <typename T, class SH, int NT, int V, int ZR, int D, bool PS>
+template <typename T, class SH, int NT, int V, int ZR, int D, bool PS, int P = 2>
 KernelEntry vec_entry(int dtype, int shape) {
     KernelEntry e;
     e.dtype = dtype;
     e.shape = shape;
     e.per_step = PS;
-    e.fn = perks_stencil_vec_kernel<T, SH, NT, V, ZR, D, PS>;
+    e.fn = perks_stencil_vec_kernel<T, SH, NT, V, ZR, D, PS, P>;
     e.nt = NT;
     e.zr = ZR;
     e.d = D;
     e.v = V;
+    e.p = P;
     return e;
 }
 

@@ -7,11 +7,17 @@ namespace perks {
 
 void register_vec_bf16_core(std::vector<KernelEntry> &out) {
     out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 0, 16, false>(PERKS_BF16, SH_3D7));
+    out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 0, 16, false, 4>(PERKS_BF16, SH_3D7));
     out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 8, 16, false>(PERKS_BF16, SH_3D7));
+    out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 8, 16, false, 4>(PERKS_BF16, SH_3D7));
     out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 0, 16, true>(PERKS_BF16, SH_3D7));
+    out.push_back(vec_entry<__nv_bfloat16, S3d7, 512, 8, 0, 16, true, 4>(PERKS_BF16, SH_3D7));
     out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 0, 16, false>(PERKS_BF16, SH_2D5));
+    out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 0, 16, false, 4>(PERKS_BF16, SH_2D5));
     out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 16, 16, false>(PERKS_BF16, SH_2D5));
+    out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 16, 16, false, 4>(PERKS_BF16, SH_2D5));
     out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 0, 16, true>(PERKS_BF16, SH_2D5));
+    out.push_back(vec_entry<__nv_bfloat16, S2d5, 256, 8, 0, 16, true, 4>(PERKS_BF16, SH_2D5));
 }
 
 }  // namespace perks

@@ -7,11 +7,17 @@ namespace perks {
 
 void register_vec_f64_core(std::vector<KernelEntry> &out) {
     out.push_back(vec_entry<double, S3d7, 512, 2, 0, 8, false>(PERKS_F64, SH_3D7));
+    out.push_back(vec_entry<double, S3d7, 512, 2, 0, 8, false, 4>(PERKS_F64, SH_3D7));
     out.push_back(vec_entry<double, S3d7, 512, 2, 8, 8, false>(PERKS_F64, SH_3D7));
+    out.push_back(vec_entry<double, S3d7, 512, 2, 8, 8, false, 4>(PERKS_F64, SH_3D7));
     out.push_back(vec_entry<double, S3d7, 512, 2, 0, 8, true>(PERKS_F64, SH_3D7));
+    out.push_back(vec_entry<double, S3d7, 512, 2, 0, 8, true, 4>(PERKS_F64, SH_3D7));
     out.push_back(vec_entry<double, S2d5, 256, 2, 0, 8, false>(PERKS_F64, SH_2D5));
+    out.push_back(vec_entry<double, S2d5, 256, 2, 0, 8, false, 4>(PERKS_F64, SH_2D5));
     out.push_back(vec_entry<double, S2d5, 256, 2, 16, 8, false>(PERKS_F64, SH_2D5));
+    out.push_back(vec_entry<double, S2d5, 256, 2, 16, 8, false, 4>(PERKS_F64, SH_2D5));
     out.push_back(vec_entry<double, S2d5, 256, 2, 0, 8, true>(PERKS_F64, SH_2D5));
+    out.push_back(vec_entry<double, S2d5, 256, 2, 0, 8, true, 4>(PERKS_F64, SH_2D5));
 }
 
 }  // namespace perks

@@ -292,3 +292,57 @@ def test_bf16_needs_vector_width(ctx):
     with pytest.raises(api.PerksError) as ei:
         st.run(2, variant=0, stats=True)
     assert ei.value.name == "UNSUPPORTED"
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["persistent", "per_step"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("name,shape,steps,tiles", [
+    ("3d7pt", (40, 36, 64), 13, (2, 3, 2)),     # 64 / 2 planes per tile: runs of 4 and remainders
+    ("3d7pt", (61, 24, 72), 7, (0, 0, 0)),      # automatic tiles, odd plane counts
+    ("2d5pt", (130, 256), 21, (0, 0, 0)),
+    ("2d5pt", (67, 128), 9, (2, 1, 3)),
+])
+def test_four_planes_per_barrier(ctx, oracle, name, shape, steps, tiles, dtype, variant):
+    """The kernels that compute 4 planes between block barriers give the same
+    bits as the low-precision oracle (fp32 / bf16) and agree with the fp64
+    oracle to 1e-12 (fp64)."""
+    from paper_2204_02064_gb300 import api
+    f = inputs.stencil_field(shape, 33)
+    offs = inputs.shape_offsets(name)
+    w = inputs.workload_weights(name, seed=5)
+    st = api.Stencil(ctx, shape, offs, w, dtype=dtype)
+    st.set_plan(tiles=tiles, planes_per_barrier=4)
+    src = torch.from_numpy(f).to(TT[dtype]).cuda()
+    st.set_field(src)
+    st.run(steps, variant=variant, stats=True)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    if dtype == "f64":
+        assert rel_err(out.cpu().numpy(), oracle.stencil_run(f, offs, w, steps)) <= 1e-12
+    else:
+        ref = oracle.stencil_run_lowp(src.float().cpu().numpy(), offs, w, steps, dtype)
+        assert np.array_equal(out.float().cpu().numpy(), ref)
+
+
+def test_step_trace(ctx, oracle):
+    """The optional step trace records, per block, a start and end time for
+    the prologue and every traced step, in order, without changing results."""
+    from paper_2204_02064_gb300 import api
+    shape = (40, 36, 64)
+    f = inputs.stencil_field(shape, 35)
+    offs, w = inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt")
+    st = api.Stencil(ctx, shape, offs, w)
+    st.set_trace(5)
+    src = torch.from_numpy(f).cuda()
+    st.set_field(src)
+    stats = st.run(8, stats=True)
+    tr = st.trace().astype(np.int64)
+    assert tr.shape == (6, stats["grid_blocks"], 2)
+    assert np.all(tr[:, :, 1] >= tr[:, :, 0])
+    # every block starts step k only after every block ended step k-1 (grid barrier)
+    assert np.all(tr[1:, :, 0].min(axis=1) >= tr[:-1, :, 1].max(axis=1))
+    out = torch.empty_like(src)
+    st.get_field(out)
+    assert rel_err(out.cpu().numpy(), oracle.stencil_run(f, offs, w, 8)) <= 1e-12
+    st.set_trace(0)
