@@ -292,14 +292,20 @@ perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t nnz, const 
                               perks_op **out);
 perks_status perks_op_destroy(perks_op *op);
 
-/* SpMV variant used inside CG and by perks_csr_spmv.  Both split the rows
+/* SpMV variant used inside CG and by perks_csr_spmv.  All split the rows
  * over blocks by the merge-path diagonal search (computed once).  Inside a
- * block, ROWVEC gives each row to 8 lanes with direct coalesced loads and one
+ * block, ROWVEC gives each row to 4 lanes with direct coalesced loads and one
  * fused multiply-add per nonzero (default); MERGE is the two-level merge-based
  * SpMV of Sec. 4.3 (thread-level diagonal search over staged tiles, which
- * also keeps A in shared memory when a block's slice fits).  Errors:
- * INVALID_ARG. */
-enum { PERKS_SPMV_ROWVEC = 0, PERKS_SPMV_MERGE = 1 };
+ * also keeps A in shared memory when a block's slice fits); SEG stages the
+ * multiplied vector in shared memory one column segment at a time, together
+ * with the block's nonzeros of that segment (bulk asynchronous copies, two
+ * buffers), so every gather is a shared-memory access -- not in the paper;
+ * its layout is built on the GPU when the kind is first selected (about 16
+ * bytes per nonzero).  Errors: INVALID_ARG; UNSUPPORTED for SEG when a block
+ * would own more than 8192 rows or a block's nonzeros in one 4096-column
+ * segment exceed 2048. */
+enum { PERKS_SPMV_ROWVEC = 0, PERKS_SPMV_MERGE = 1, PERKS_SPMV_SEG = 2 };
 perks_status perks_op_set_spmv(perks_op *op, int32_t kind);
 
 /* y = A x for device vectors of n doubles (one launch). */

@@ -19,7 +19,7 @@ MAX_POINTS = 125
 F64, F32, BF16 = 0, 1, 2
 PERSISTENT, PER_STEP = 0, 1
 CG_FP64, CG_FP32_IR, CG_FP64_MULTI = 0, 1, 2
-SPMV_ROWVEC, SPMV_MERGE = 0, 1
+SPMV_ROWVEC, SPMV_MERGE, SPMV_SEG = 0, 1, 2
 
 STATUS = {
     0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "OUT_OF_MEMORY",
@@ -426,7 +426,9 @@ class CsrOperator:
         self.nnz = nnz
 
     def set_spmv(self, kind: int):
-        """SPMV_ROWVEC (default) or SPMV_MERGE (thread-level merge walk)."""
+        """SPMV_ROWVEC (default), SPMV_MERGE (thread-level merge walk) or
+        SPMV_SEG (vector and nonzeros staged in shared memory one column
+        segment at a time; its layout is built on first selection)."""
         self.ctx.check(self._lib.perks_op_set_spmv(self.handle, int(kind)))
 
     def spmv(self, x, y, stream=None):

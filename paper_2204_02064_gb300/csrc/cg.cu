@@ -186,6 +186,83 @@ __global__ void cast_to_f32(const double *__restrict__ v, float *__restrict__ o,
         o[i] = (float)v[i];
 }
 
+// ------------------------------------------- column-segmented SpMV layout
+
+// Thread (g, w) walks the rows of block g owned by warp w (local index = w
+// mod kSegWarps) in increasing order, and each row's nonzeros in column order,
+// so the nonzeros of every (block, segment, warp) bucket are visited in the
+// order the layout stores them.  Pass 0 counts, pass 1 scatters.
+template <int PASS>
+__global__ void seg_walk_kernel(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                const double *__restrict__ val, const int *__restrict__ part_row, int G, int nseg,
+                                unsigned *cnt, const unsigned *tile_off, const unsigned short *wofs,
+                                double *sval, float *sval32, unsigned short *scol, unsigned short *srow) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G * kSegWarps) return;
+    const int g = t / kSegWarps, w = t % kSegWarps;
+    const int r0 = part_row[g], r1 = part_row[g + 1];
+    for (int rl = w; rl < r1 - r0; rl += kSegWarps) {
+        const int r = r0 + rl;
+        for (int j = rowptr[r]; j < rowptr[r + 1]; ++j) {
+            const int c = col[j];
+            const int sg = c / kSegWidth;
+            const long long tile = (long long)g * nseg + sg;
+            unsigned *cur = cnt + tile * kSegWarps + w;
+            if (PASS == 0) {
+                ++*cur;
+            } else {
+                const unsigned pos = tile_off[tile] + wofs[tile * kSegOfsPad + w] + (*cur)++;
+                sval[pos] = val[j];
+                sval32[pos] = (float)val[j];
+                scol[pos] = (unsigned short)(c - sg * kSegWidth);
+                srow[pos] = (unsigned short)rl;
+            }
+        }
+    }
+}
+
+// Tile lengths, warp offsets and tile starts (each rounded up to 8 nonzeros
+// so every slice of the layout starts on a 16-byte boundary); one block.
+__global__ void seg_tiles_kernel(const unsigned *cnt, long long ntiles, unsigned short *wofs, unsigned *tile_off,
+                                 unsigned long long *total, unsigned *max_len) {
+    __shared__ unsigned long long s_sum[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const long long per = (ntiles + nt - 1) / nt;
+    const long long t0 = tid * per, t1 = min(ntiles, t0 + per);
+    unsigned long long local = 0;
+    unsigned mx = 0;
+    for (long long t = t0; t < t1; ++t) {
+        unsigned acc = 0;
+        for (int w = 0; w < kSegWarps; ++w) {
+            const unsigned c = cnt[t * kSegWarps + w];
+            wofs[t * kSegOfsPad + w] = (unsigned short)min(acc, 65535u);
+            acc += c;
+        }
+        wofs[t * kSegOfsPad + kSegWarps] = (unsigned short)min(acc, 65535u);
+        for (int w = kSegWarps + 1; w < kSegOfsPad; ++w) wofs[t * kSegOfsPad + w] = 0;
+        mx = max(mx, acc);
+        local += (acc + 7u) & ~7u;
+    }
+    s_sum[tid] = local;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < nt; ++i) {
+            const unsigned long long v = s_sum[i];
+            s_sum[i] = run;
+            run += v;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    unsigned long long off = s_sum[tid];
+    for (long long t = t0; t < t1; ++t) {
+        tile_off[t] = (unsigned)min(off, 0xFFFFFFFFull);
+        off += (wofs[t * kSegOfsPad + kSegWarps] + 7u) & ~7u;
+    }
+    atomicMax(max_len, mx);
+}
+
 }  // namespace
 
 struct perks_op {
@@ -201,6 +278,13 @@ struct perks_op {
     int G2 = 0;                                         // row-vector kernel: G2 blocks
     int *part_row2 = nullptr, *part_ntiles2 = nullptr;
     int2 *part_tiles2 = nullptr;
+    // column-segmented SpMV: G blocks (part_row), layout built on first use
+    bool seg_built = false;
+    int nseg = 0;
+    double *sval = nullptr;
+    float *sval32 = nullptr;
+    unsigned short *scol = nullptr, *srow = nullptr, *swofs = nullptr;
+    unsigned *stile_off = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
     double *part = nullptr;
@@ -229,7 +313,8 @@ template <typename T> perks_status dalloc(perks_context *ctx, T **p, size_t coun
 void free_op(perks_op *op) {
     void *ptrs[] = {op->rowptr, op->col, op->val, op->val32, op->part_row, op->part_ntiles,
                     op->part_tiles, op->part_row2, op->part_ntiles2, op->part_tiles2, op->b, op->x, op->r, op->p, op->q, op->r32, op->p32,
-                    op->q32, op->d32, op->part, op->trace, op->res, op->ms, op->bar, op->err};
+                    op->q32, op->d32, op->part, op->trace, op->res, op->ms, op->bar, op->err,
+                    op->sval, op->sval32, op->scol, op->srow, op->swofs, op->stile_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (op->ms_done_host) cudaFreeHost(op->ms_done_host);
@@ -245,7 +330,7 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.val = op->val;
     a.val32 = op->val32;
     const bool rv = op->spmv_kind == PERKS_SPMV_ROWVEC;
-    a.part_row = rv ? op->part_row2 : op->part_row;
+    a.part_row = rv ? op->part_row2 : op->part_row;  // merge and segmented kinds: G blocks
     a.part_ntiles = rv ? op->part_ntiles2 : op->part_ntiles;
     a.part_tiles = rv ? op->part_tiles2 : op->part_tiles;
     a.b = op->b;
@@ -262,6 +347,13 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.mode = mode;
     a.allow_cache = 1;
     a.spmv_kind = op->spmv_kind;
+    a.seg.nseg = op->nseg;
+    a.seg.val = op->sval;
+    a.seg.val32 = op->sval32;
+    a.seg.col = op->scol;
+    a.seg.row = op->srow;
+    a.seg.tile_off = op->stile_off;
+    a.seg.wofs = op->swofs;
     a.bar = op->bar;
     a.err = op->err;
     a.timeout_ns = op->ctx->timeout_ns;
@@ -272,20 +364,27 @@ perks_status configure(perks_op *op) {
     if (op->configured) return PERKS_OK;
     perks_context *ctx = op->ctx;
     const int smem = (int)cg_smem_bytes();
-    PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)perks_cg_kernel<false>,
+    PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)perks_cg_kernel<1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)perks_cg_kernel<2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem_bytes()));
     PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)cg_multi_spmv,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_cg_kernel<false>,
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_cg_kernel<1>,
                                                                   kCgThreads, smem));
     if (per_sm < 1 || per_sm * ctx->sm_count < op->G)
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G);
     int per_sm2 = 0;
-    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void *)perks_cg_kernel<true>,
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void *)perks_cg_kernel<0>,
                                                                   kCgThreads, kCgRowvecSmem));
     if (per_sm2 < 1 || per_sm2 * ctx->sm_count < op->G2)
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G2);
+    int per_sm3 = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, (const void *)perks_cg_kernel<2>,
+                                                                  kCgThreads, seg_smem_bytes()));
+    if (per_sm3 < 1 || per_sm3 * ctx->sm_count < op->G)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G);
     op->configured = true;
     return PERKS_OK;
 }
@@ -296,10 +395,13 @@ perks_status launch_persistent(perks_op *op, const CgArgs &a, cudaStream_t s) {
     PERKS_CUDA(ctx, cudaMemsetAsync(op->err, 0, sizeof(DevError), s));
     void *args[] = {(void *)&a};
     if (op->spmv_kind == PERKS_SPMV_ROWVEC)
-        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<true>, dim3(op->G2),
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<0>, dim3(op->G2),
                                                     dim3(kCgThreads), args, kCgRowvecSmem, s));
+    else if (op->spmv_kind == PERKS_SPMV_SEG)
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<2>, dim3(op->G),
+                                                    dim3(kCgThreads), args, seg_smem_bytes(), s));
     else
-        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<false>, dim3(op->G),
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<1>, dim3(op->G),
                                                     dim3(kCgThreads), args, cg_smem_bytes(), s));
     return PERKS_OK;
 }
@@ -389,6 +491,82 @@ perks_status read_result(perks_op *op, cudaStream_t s, perks_cg_stats *stats) {
 }  // namespace
 
 // ======================================================================= ABI
+
+namespace {
+
+// Builds the column-segmented layout (once per operator).  UNSUPPORTED when a
+// block has more rows than its shared-memory accumulators hold or a tile
+// more nonzeros than a segment buffer.
+perks_status build_seg(perks_op *op) {
+    if (op->seg_built) return PERKS_OK;
+    perks_context *ctx = op->ctx;
+    const int G = op->G;
+    std::vector<int> pr((size_t)G + 1);
+    PERKS_CUDA(ctx, cudaMemcpy(pr.data(), op->part_row, sizeof(int) * ((size_t)G + 1), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < G; ++g)
+        if (pr[g + 1] - pr[g] > kSegMaxRows)
+            return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                        "segmented SpMV: block %d has %d rows (at most %d)", g, pr[g + 1] - pr[g], kSegMaxRows);
+    const int nseg = (op->n + kSegWidth - 1) / kSegWidth;
+    const long long ntiles = (long long)G * nseg;
+    unsigned *cnt = nullptr, *max_len = nullptr;
+    unsigned long long *total = nullptr;
+    perks_status rc = PERKS_OK;
+    auto cleanup = [&]() {
+        if (cnt) cudaFree(cnt);
+        if (max_len) cudaFree(max_len);
+        if (total) cudaFree(total);
+    };
+    if ((rc = dalloc(ctx, &cnt, (size_t)ntiles * kSegWarps)) || (rc = dalloc(ctx, &max_len, 1)) ||
+        (rc = dalloc(ctx, &total, 1)) || (rc = dalloc(ctx, &op->swofs, (size_t)ntiles * kSegOfsPad)) ||
+        (rc = dalloc(ctx, &op->stile_off, (size_t)ntiles))) {
+        cleanup();
+        return rc;
+    }
+    cudaError_t e = cudaMemset(cnt, 0, sizeof(unsigned) * (size_t)ntiles * kSegWarps);
+    if (e == cudaSuccess) e = cudaMemset(max_len, 0, sizeof(unsigned));
+    const int threads = G * kSegWarps;
+    if (e == cudaSuccess) {
+        seg_walk_kernel<0><<<(threads + 127) / 128, 128>>>(op->rowptr, op->col, op->val, op->part_row, G, nseg, cnt,
+                                                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        seg_tiles_kernel<<<1, 1024>>>(cnt, ntiles, op->swofs, op->stile_off, total, max_len);
+        e = cudaGetLastError();
+    }
+    unsigned long long tot = 0;
+    unsigned mx = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&mx, max_len, sizeof(mx), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "segmented SpMV layout"); }
+    if (mx > (unsigned)kSegCap || tot >= 0xFFFFFFF0ull) {
+        cleanup();
+        return fail(ctx, PERKS_ERR_UNSUPPORTED, "segmented SpMV: a tile holds %u nonzeros (at most %d)", mx, kSegCap);
+    }
+    const size_t ne = (size_t)tot + 8;
+    if ((rc = dalloc(ctx, &op->sval, ne)) || (rc = dalloc(ctx, &op->sval32, ne)) || (rc = dalloc(ctx, &op->scol, ne)) ||
+        (rc = dalloc(ctx, &op->srow, ne))) {
+        cleanup();
+        return rc;
+    }
+    e = cudaMemset(op->sval, 0, sizeof(double) * ne);
+    if (e == cudaSuccess) e = cudaMemset(op->sval32, 0, sizeof(float) * ne);
+    if (e == cudaSuccess) e = cudaMemset(op->scol, 0, sizeof(unsigned short) * ne);
+    if (e == cudaSuccess) e = cudaMemset(op->srow, 0, sizeof(unsigned short) * ne);
+    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned) * (size_t)ntiles * kSegWarps);
+    if (e == cudaSuccess) {
+        seg_walk_kernel<1><<<(threads + 127) / 128, 128>>>(op->rowptr, op->col, op->val, op->part_row, G, nseg, cnt,
+                                                           op->stile_off, op->swofs, op->sval, op->sval32, op->scol,
+                                                           op->srow);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "segmented SpMV layout");
+    op->nseg = nseg;
+    op->seg_built = true;
+    return PERKS_OK;
+}
+
+}  // namespace
 
 extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t nnz, const int32_t *rowptr,
                                          const int32_t *col, const double *val, int on_device,
@@ -523,6 +701,12 @@ extern "C" perks_status perks_csr_spmv(perks_op *op, const double *x, double *y,
     CgArgs a = make_args(op, 0.0, 0, CGK_SPMV, 0.0);
     a.spmv_in = x;
     a.spmv_out = y;
+    if (op->spmv_kind == PERKS_SPMV_SEG) {
+        // the segment copies read whole 16-byte units: stage x into a padded vector
+        PERKS_CUDA(op->ctx, cudaMemcpyAsync(op->p, x, sizeof(double) * (size_t)op->n, cudaMemcpyDeviceToDevice,
+                                            (cudaStream_t)stream));
+        a.spmv_in = op->p;
+    }
     return launch_persistent(op, a, (cudaStream_t)stream);
 }
 
@@ -571,8 +755,14 @@ extern "C" perks_status perks_cg_last_result(perks_op *op, perks_stream stream, 
 
 extern "C" perks_status perks_op_set_spmv(perks_op *op, int32_t kind) {
     if (!op) return PERKS_ERR_INVALID_ARG;
-    if (kind != PERKS_SPMV_ROWVEC && kind != PERKS_SPMV_MERGE)
+    if (kind != PERKS_SPMV_ROWVEC && kind != PERKS_SPMV_MERGE && kind != PERKS_SPMV_SEG)
         return fail(op->ctx, PERKS_ERR_INVALID_ARG, "op_set_spmv: unknown kind %d", kind);
+    if (kind == PERKS_SPMV_SEG) {
+        perks_status rc = use_device(op->ctx);
+        if (rc) return rc;
+        rc = build_seg(op);
+        if (rc) return rc;
+    }
     op->spmv_kind = kind;
     return PERKS_OK;
 }

@@ -29,6 +29,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "cg_seg.cuh"
 
 namespace perks {
 
@@ -72,9 +73,10 @@ struct CgArgs {
     double inner_rtol;
     int mode;
     int allow_cache;
-    int spmv_kind;           // 0: row-vector SpMV (default), 1: thread-level merge walk
+    int spmv_kind;           // 0: row-vector SpMV (default), 1: thread-level merge walk, 2: column-segmented
     const double *spmv_in;
     double *spmv_out;
+    SegArgs seg;             // column-segmented layout (spmv_kind 2)
     unsigned long long *bar;
     DevError *err;
     long long timeout_ns;
@@ -418,6 +420,23 @@ __device__ __forceinline__ double spmv_any(const CgArgs &a, const CgSmem &s, con
     return spmv_block<V>(a, s, sl, gval, vin, vout, dotv);
 }
 
+template <typename V> __device__ __forceinline__ const V *seg_vals(const SegArgs &g);
+template <> __device__ __forceinline__ const double *seg_vals<double>(const SegArgs &g) { return g.val; }
+template <> __device__ __forceinline__ const float *seg_vals<float>(const SegArgs &g) { return g.val32; }
+
+// The SpMV of kernel kind KIND (0 row-vector, 1 merge walk, 2 column-segmented).
+template <int KIND, typename V>
+__device__ __forceinline__ double spmv_k(const CgArgs &a, const CgSmem &s, const CgSlice &sl, const V *gval,
+                                         const V *vin, V *vout, const V *dotv, unsigned char *smem, SegState &st) {
+    if constexpr (KIND == 2) {
+        bool ok;
+        return spmv_seg<V>(a.seg, a.n, sl.r0, sl.r1, seg_vals<V>(a.seg), vin, vout, dotv, smem, st, s.red, a.err,
+                           a.timeout_ns, ok);
+    } else {
+        return spmv_any<V>(a, s, sl, gval, vin, vout, dotv);
+    }
+}
+
 __device__ __forceinline__ bool cg_sync(const CgArgs &a, unsigned long long &epoch) {
     return grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns);
 }
@@ -429,13 +448,27 @@ constexpr size_t kCgRowvecSmem = 1024;
 // ROWVEC: row-vector SpMV only, 1 KB of shared memory and at most 64
 // registers, so two blocks share an SM (twice the loads in flight); otherwise
 // the merge-based SpMV with its staged tiles, one block per SM.
-template <bool ROWVEC>
-__global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(const __grid_constant__ CgArgs a) {
+template <int KIND>
+__global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel(const __grid_constant__ CgArgs a) {
+    constexpr bool ROWVEC = KIND != 1;  // no merge-walk tiles in shared memory
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CgSmem s;
-    if constexpr (ROWVEC) {
+    SegState st;
+    st.bar = nullptr;
+    st.parity = 0;
+    if constexpr (KIND == 0) {
         std::memset(&s, 0, sizeof(s));
         s.red = reinterpret_cast<double *>(smem_raw);
+    } else if constexpr (KIND == 2) {
+        std::memset(&s, 0, sizeof(s));
+        s.red = reinterpret_cast<double *>(smem_raw + 2 * seg_buf_bytes() + (size_t)kSegMaxRows * sizeof(double));
+        st.bar = reinterpret_cast<unsigned long long *>(s.red + 64);
+        if (threadIdx.x == 0) {
+            mbar_init(&st.bar[0], 1);
+            mbar_init(&st.bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
     } else {
         s = carve_cg_smem(smem_raw);
     }
@@ -460,7 +493,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
     }
 
     if (a.mode == CGK_SPMV) {
-        spmv_any<double>(a, s, sl, a.val, a.spmv_in, a.spmv_out, nullptr);
+        spmv_k<KIND, double>(a, s, sl, a.val, a.spmv_in, a.spmv_out, nullptr, smem_raw, st);
         return;
     }
 
@@ -469,7 +502,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
     double *x = a.x, *r = a.r, *p = a.p, *q = a.q;
 
     // ---- r0 = b - A x0, ||b||^2
-    spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
+    spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);
     double bb_p = 0.0, rr_p = 0.0;
     for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
         const double ri = b[i] - q[i];
@@ -496,7 +529,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
             bool converged = false;
             while (it < a.max_iter) {
                 // A: q = A p, <p, q>
-                const double pq_p = spmv_any<double>(a, s, sl, a.val, p, q, p);
+                const double pq_p = spmv_k<KIND, double>(a, s, sl, a.val, p, q, p, smem_raw, st);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 // B: alpha; x += alpha p; r -= alpha q; <r, r>
@@ -529,7 +562,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             // C5: true residual in fp64
-            spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
+            spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);
             double tr_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
                 const double ri = b[i] - q[i];
@@ -567,7 +600,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
             const double itol2 = a.inner_rtol * a.inner_rtol * irr;
             if (!cg_sync(a, epoch)) return;
             while (it < a.max_iter) {
-                const double pq_p = spmv_any<float>(a, s, sl, a.val32, p32, q32, p32);
+                const double pq_p = spmv_k<KIND, float>(a, s, sl, a.val32, p32, q32, p32, smem_raw, st);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 const double pq = grid_sum(part0, G, s.red);
@@ -596,7 +629,7 @@ __global__ void __launch_bounds__(kCgThreads, ROWVEC ? 2 : 1) perks_cg_kernel(co
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) x[i] += (double)d32[i];
             ++outer;
             if (!cg_sync(a, epoch)) return;
-            spmv_any<double>(a, s, sl, a.val, x, q, nullptr);
+            spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);
             double tr_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
                 const double ri = b[i] - q[i];

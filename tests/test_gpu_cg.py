@@ -52,14 +52,14 @@ def _spmv_case(ctx, oracle, rp, c, v, seed, kind=0):
     assert np.max(np.abs(y.cpu().numpy() - ref) / scale) <= 1e-13
 
 
-@pytest.mark.parametrize("kind", [0, 1], ids=["rowvec", "merge"])
+@pytest.mark.parametrize("kind", [0, 1, 2], ids=["rowvec", "merge", "seg"])
 @pytest.mark.parametrize("n,seed", [(7, 1), (2000, 2), (50000, 3), (300001, 4)])
 def test_spmv_synthetic(ctx, oracle, n, seed, kind):
     rp, c, v = inputs.csr_spd_matrix(n, seed)
     _spmv_case(ctx, oracle, rp, c, v, seed, kind)
 
 
-@pytest.mark.parametrize("kind", [0, 1], ids=["rowvec", "merge"])
+@pytest.mark.parametrize("kind", [0, 1, 2], ids=["rowvec", "merge", "seg"])
 def test_spmv_long_rows_and_empty_rows(ctx, oracle, kind):
     """Rows longer than a tile (4096 path items) and empty rows exercise the
     thread- and tile-level carry fix-up."""
@@ -67,9 +67,16 @@ def test_spmv_long_rows_and_empty_rows(ctx, oracle, kind):
     n = 30000
     lengths = rng.integers(0, 40, size=n)
     lengths[::97] = 0
-    lengths[123] = 20000
-    lengths[5000] = 9000
-    lengths[5001] = 4097
+    if kind == 2:
+        # the segmented layout caps a block's nonzeros per 4096-column segment
+        # at 2048: long rows spread over the segments
+        lengths[123] = 12000
+        lengths[5000] = 6000
+        lengths[5001] = 4097
+    else:
+        lengths[123] = 20000
+        lengths[5000] = 9000
+        lengths[5001] = 4097
     rp = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(lengths, out=rp[1:])
     nnz = int(rp[-1])
@@ -100,7 +107,7 @@ def _solve(ctx, rp, c, v, b, mode, rtol=1e-10, x0=None, host=False, trace_len=0,
     return x.cpu().numpy(), res
 
 
-@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
+@pytest.mark.parametrize("spmv", [0, 1, 2], ids=["rowvec", "merge", "seg"])
 @pytest.mark.parametrize("mode", [0, 2], ids=["persistent", "multi_launch"])
 def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode, spmv):
     rp, c, v, b = system_4k
@@ -114,7 +121,7 @@ def test_cg_fp64_trace_and_solution(ctx, oracle, system_4k, mode, spmv):
     assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
 
 
-@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
+@pytest.mark.parametrize("spmv", [0, 1, 2], ids=["rowvec", "merge", "seg"])
 def test_cg_fp32_ir(ctx, oracle, system_4k, spmv):
     from paper_2204_02064_gb300 import api
     rp, c, v, b = system_4k
@@ -136,7 +143,7 @@ def test_cg_host_buffers_and_initial_guess(ctx, oracle, system_4k):
     assert np.linalg.norm(x - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
 
 
-@pytest.mark.parametrize("spmv", [0, 1], ids=["rowvec", "merge"])
+@pytest.mark.parametrize("spmv", [0, 1, 2], ids=["rowvec", "merge", "seg"])
 def test_cg_cached_and_streamed_agree(ctx, oracle, spmv):
     # n=2000: every block's slice fits in shared memory (cached A, merge path);
     # n=60000: several tiles per block, streamed each iteration.
@@ -192,17 +199,41 @@ def system_full():
     return rp, c, v, inputs.cg_rhs(n, inputs.SEED_CG)
 
 
-def test_cg_full_size(ctx, oracle, system_full):
+@pytest.mark.parametrize("spmv", [0, 2], ids=["rowvec", "seg"])
+def test_cg_full_size(ctx, oracle, system_full, spmv):
     """The CG workload at full size (n = 2^20, rtol 1e-10): trace of the first
     5 iterations against the oracle, true residual on the GPU side, both
     modes."""
     from paper_2204_02064_gb300 import api
     rp, c, v, b = system_full
     ref = oracle.cg(rp, c, v, b, rtol=1e-10, max_iter=5, max_restarts=0, trace_len=5)
-    _, res5 = _solve(ctx, rp, c, v, b, 0, max_iter=5, trace_len=5, raise_on_error=False)
+    _, res5 = _solve(ctx, rp, c, v, b, 0, max_iter=5, trace_len=5, raise_on_error=False, spmv=spmv)
     assert np.max(np.abs(res5["trace"] - ref["trace"]) / np.abs(ref["trace"])) <= 1e-11
-    x, res = _solve(ctx, rp, c, v, b, 0)
+    x, res = _solve(ctx, rp, c, v, b, 0, spmv=spmv)
     assert res["true_rel_residual"] <= 1e-10
-    x2, res2 = _solve(ctx, rp, c, v, b, api.CG_FP32_IR)
+    x2, res2 = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, spmv=spmv)
     assert res2["true_rel_residual"] <= 1e-10
     assert np.linalg.norm(x - x2) <= 1e-7 * np.linalg.norm(x)
+
+
+def test_seg_spmv_limits_reported(ctx):
+    """A block whose nonzeros in one 4096-column segment exceed the 2048 the
+    shared-memory buffers hold cannot use the segmented SpMV: UNSUPPORTED,
+    and the operator keeps working with its previous kind."""
+    from paper_2204_02064_gb300 import api
+    n = 3000
+    # row 0: its diagonal; row 1: 2500 nonzeros in columns 0..2499 (one
+    # segment); rows 2..n-1: their diagonal
+    lengths = np.ones(n, dtype=np.int64)
+    lengths[1] = 2500
+    rp = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    cols = np.concatenate([[0], np.arange(2500), np.arange(2, n)]).astype(np.int32)
+    vals = np.ones(cols.shape[0])
+    op = api.CsrOperator(ctx, _dev(rp), _dev(cols), _dev(vals))
+    with pytest.raises(api.PerksError) as ei:
+        op.set_spmv(2)
+    assert ei.value.name == "UNSUPPORTED"
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    op.spmv(_dev(np.ones(n)), y)
+    torch.cuda.synchronize()
+    assert y[1].item() == 2500.0
