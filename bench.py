@@ -124,14 +124,19 @@ def _max_over_ranks(world, v):
     return float(t.item())
 
 
-def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1):
-    """Times K runs of `steps` Jacobi steps; returns dict with per-run ms."""
+def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1, tune=True):
+    """Times K runs of `steps` Jacobi steps (plan chosen by the autotuner for
+    this variant first); returns dict with per-run ms."""
     from paper_2204_02064_gb300 import inputs
     shape = (L, L, L)
     f = torch.from_numpy(inputs.stencil_field(shape, seed)).to(
-        {"f64": torch.float64, "f32": torch.float32}[dtype]).cuda()
+        {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]).cuda()
     st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
                      dtype=dtype)
+    tuned = None
+    if tune:
+        st.set_field(f)
+        tuned = st.autotune(variant, probe_steps=10)
     desc = st.describe(steps, variant)
     stream = torch.cuda.current_stream()
     for _ in range(W):
@@ -150,13 +155,15 @@ def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1):
         times.append(e0.elapsed_time(e1))
     st.check()
     st.close()
-    return {"ms": times, "desc": desc, "cells": L ** 3}
+    return {"ms": times, "desc": desc, "cells": L ** 3, "plan": tuned}
 
 
 def stencil2d_leg(api, torch, ctx, L, steps, variant, K, W):
     from paper_2204_02064_gb300 import inputs
     f = torch.from_numpy(inputs.stencil_field((L, L), inputs.SEED_2D)).cuda()
     st = api.Stencil(ctx, (L, L), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"))
+    st.set_field(f)
+    st.autotune(variant, probe_steps=20)
     stream = torch.cuda.current_stream()
     for _ in range(W):
         st.set_field(f)
@@ -184,6 +191,8 @@ def e2e_leg(api, torch, ctx, L, steps, K, W):
     host_out = torch.empty_like(host_in).pin_memory()
     st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
     stream = torch.cuda.current_stream()
+    st.set_field(host_in, stream)
+    st.autotune(0, probe_steps=10)
     for _ in range(W):
         st.set_field(host_in, stream)
         st.run(steps, 0, stream)
@@ -457,6 +466,8 @@ def main():
     shape = (L_3D, L_3D, L_3D)
     f = torch.from_numpy(inputs.stencil_field(shape, 1)).cuda()
     st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+    st.set_field(f)
+    tuned = st.autotune(api.PERSISTENT, probe_steps=10)
     desc = st.describe(STEPS_3D, api.PERSISTENT)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -515,14 +526,14 @@ def main():
         try:
             ps = stencil_leg(api, torch, ctx, L_3D, STEPS_3D, "f64", api.PER_STEP, 2, 1)
             variants["3d7pt_384_f64_per_step_baseline"] = {
-                "gcells": cells / (min(ps["ms"]) * 1e-3) / 1e9, "ms": min(ps["ms"])}
+                "gcells": cells / (min(ps["ms"]) * 1e-3) / 1e9, "ms": min(ps["ms"]), "plan": ps["plan"]}
             # the 2-D workload (2d5pt fp64 256^2, 100 steps): barrier-dominated
             for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
                 r = stencil2d_leg(api, torch, ctx, 256, 100, var, 5, 2)
                 variants[f"2d5pt_256_f64_{vname}"] = {
                     "gcells": 256 * 256 * 100 / (min(r) * 1e-3) / 1e9, "ms": min(r),
                     "us_per_step": min(r) * 1e3 / 100}
-            for L, dt in ((192, "f64"), (192, "f32"), (384, "f32")):
+            for L, dt in ((192, "f64"), (192, "f32"), (192, "bf16"), (384, "f32"), (384, "bf16")):
                 for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
                     r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, var, 2, 1)
                     c = float(L ** 3) * STEPS_3D
@@ -531,7 +542,7 @@ def main():
                     variants[f"3d7pt_{L}_{dt}_{vname}"] = {
                         "gcells": c / (ms * 1e-3) / 1e9, "ms": ms,
                         "algorithmic_gbs": d["algorithmic_bytes"] / (ms * 1e-3) / 1e9,
-                        "cached_fraction": d["cached_cells"] / max(d["cells"], 1)}
+                        "cached_fraction": d["cached_cells"] / max(d["cells"], 1), "plan": r["plan"]}
         except Exception as e:
             variants["stencil_error"] = str(e)
         try:
@@ -562,10 +573,11 @@ def main():
                                    "uniform[0,1) seeded; one persistent cooperative launch",
                        "l2": "inputs larger than L2 (2 x 453 MB ping-pong)",
                        "parallelism": f"replicas x{world}",
-                       "plan": {k: desc[k] for k in ("grid_blocks", "threads_per_block", "tiles_x",
-                                                    "tiles_y", "tiles_z", "reg_cache_planes",
-                                                    "smem_cache_planes", "cached_cells",
-                                                    "halo_cells_per_step")}},
+                       "plan": {**{k: desc[k] for k in ("grid_blocks", "threads_per_block", "tiles_x",
+                                                       "tiles_y", "tiles_z", "reg_cache_planes",
+                                                       "smem_cache_planes", "cached_cells",
+                                                       "halo_cells_per_step")},
+                                "planes_per_barrier": tuned["planes_per_barrier"], "autotuned": True}},
             "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": tflops / fp64_peak, "traffic": traffic,
                          "peak_kind": "derived: 152 SMs x 2 fp64 FMA/clk x 2 FLOP x max SM clock "

@@ -156,6 +156,18 @@ perks_status perks_stencil_set_trace(perks_stencil *st, int32_t steps);
 perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t capacity,
                                      int32_t *grid_blocks, int32_t *steps);
 
+/* Autotuner (not in the paper): times candidate plans for `variant` on the
+ * stencil's current field for `probe_steps` (>= 2) steps each -- the model's
+ * own tiling and up to six tilings ranked by tz * (1 + halo fraction), each
+ * with and without the register cache and with 2 or 4 planes per block
+ * barrier -- restores the field, installs the fastest plan (as
+ * perks_stencil_set_plan would) and returns it with its time per step.
+ * Synchronizes `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY,
+ * CUDA, BARRIER_TIMEOUT. */
+perks_status perks_stencil_autotune(perks_stencil *st, int32_t variant, int32_t probe_steps,
+                                    perks_stream stream, perks_stencil_plan *chosen,
+                                    double *ms_per_step);
+
 /* Plan override (NULL resets to automatic).  Errors: INVALID_ARG,
  * UNSUPPORTED (the persistent kernel cannot host the requested tiles). */
 perks_status perks_stencil_set_plan(perks_stencil *st, const perks_stencil_plan *plan);
@@ -403,6 +415,12 @@ int32_t perks_warmnet_num_params(const perks_warmnet *net);
 /* Copy the fp32 parameters to / from a host array of num_params floats. */
 perks_status perks_warmnet_get_params(perks_warmnet *net, float *host);
 perks_status perks_warmnet_set_params(perks_warmnet *net, const float *host);
+/* Coarse-grid mode (factor 1..32, default 1): the inputs log k and f are
+ * averaged over factor x factor blocks, the network runs on that coarser
+ * grid (training targets u averaged the same way), and predict() returns the
+ * bilinear interpolation of its output at the fine cell centres; grids must
+ * then be divisible by the factor (else INVALID_ARG). */
+perks_status perks_warmnet_set_pool(perks_warmnet *net, int32_t factor);
 /* Output scale (> 0): the network predicts u / scale. */
 perks_status perks_warmnet_set_scale(perks_warmnet *net, float scale);
 float perks_warmnet_get_scale(const perks_warmnet *net);

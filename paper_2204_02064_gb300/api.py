@@ -126,6 +126,7 @@ def _declare(lib):
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_op_set_spmv": ([P, i32], i32),
         "perks_stencil_set_trace": ([P, i32], i32),
+        "perks_stencil_autotune": ([P, i32, i32, P, ctypes.POINTER(StencilPlan), ctypes.POINTER(f64)], i32),
         "perks_stencil_get_trace": ([P, P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "perks_poisson_create": ([P, i32, i32, i32, P, ctypes.c_int, ctypes.POINTER(P)], i32),
         "perks_poisson_destroy": ([P], i32),
@@ -138,6 +139,7 @@ def _declare(lib):
         "perks_warmnet_set_params": ([P, P], i32),
         "perks_warmnet_set_scale": ([P, ctypes.c_float], i32),
         "perks_warmnet_get_scale": ([P], ctypes.c_float),
+        "perks_warmnet_set_pool": ([P, i32], i32),
         "perks_warmnet_predict": ([P, i32, i32, i32, P, P, P, P], i32),
         "perks_warmnet_gradient": ([P, i32, i32, i32, P, P, P, P, P, P], i32),
         "perks_warmnet_train_step": ([P, i32, i32, i32, P, P, P, ctypes.c_float, P, P], i32),
@@ -332,6 +334,16 @@ class Stencil:
         p.reserved[0] = 1 if scalar else 0
         p.reserved[1] = int(planes_per_barrier)
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
+
+    def autotune(self, variant: int = PERSISTENT, probe_steps: int = 10, stream=None) -> dict:
+        """Times candidate plans on the current field (restored afterwards),
+        installs the fastest and returns it with its time per step."""
+        p = StencilPlan()
+        ms = ctypes.c_double()
+        self.ctx.check(self._lib.perks_stencil_autotune(self.handle, int(variant), int(probe_steps),
+                                                        _stream(stream), ctypes.byref(p), ctypes.byref(ms)))
+        return {"tiles": (p.tiles_x, p.tiles_y, p.tiles_z), "reg_cache": p.reg_cache,
+                "planes_per_barrier": p.reserved[1], "ms_per_step": ms.value}
 
     def set_trace(self, steps: int):
         """Record per-block start/end times of the first ``steps`` steps of the
@@ -607,7 +619,7 @@ class WarmNet:
     mapping (log k, f) to a first guess of u.  Images are device float64
     tensors of shape (nimg, ny, nx)."""
 
-    def __init__(self, ctx: Context, storage: int = BF16, dilations=(1, 2, 4, 8), seed: int = 0):
+    def __init__(self, ctx: Context, storage: int = BF16, dilations=(1, 2, 4, 8), seed: int = 0, pool: int = 1):
         self.ctx = ctx
         self._lib = ctx._lib
         d = np.ascontiguousarray(dilations, dtype=np.int32)
@@ -616,6 +628,9 @@ class WarmNet:
                                                  ctypes.byref(h)))
         self.handle = h
         self.num_params = int(self._lib.perks_warmnet_num_params(h))
+        self.pool = int(pool)
+        if self.pool != 1:
+            ctx.check(self._lib.perks_warmnet_set_pool(h, self.pool))
 
     def close(self):
         if getattr(self, "handle", None):

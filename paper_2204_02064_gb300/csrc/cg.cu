@@ -196,15 +196,21 @@ template <int PASS>
 __global__ void seg_walk_kernel(const int *__restrict__ rowptr, const int *__restrict__ col,
                                 const double *__restrict__ val, const int *__restrict__ part_row, int G, int nseg,
                                 unsigned *cnt, const unsigned *tile_off, const unsigned short *wofs,
-                                double *sval, float *sval32, unsigned short *scol, unsigned short *srow) {
+                                double *sval, float *sval32, unsigned short *scol, unsigned short *srow,
+                                double *sdiag, float *sdiag32) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= G * kSegWarps) return;
     const int g = t / kSegWarps, w = t % kSegWarps;
     const int r0 = part_row[g], r1 = part_row[g + 1];
     for (int rl = w; rl < r1 - r0; rl += kSegWarps) {
         const int r = r0 + rl;
+        double dsum = 0.0;
         for (int j = rowptr[r]; j < rowptr[r + 1]; ++j) {
             const int c = col[j];
+            if (c == r) {  // diagonal: kept per row, applied after the segments
+                dsum += val[j];
+                continue;
+            }
             const int sg = c / kSegWidth;
             const long long tile = (long long)g * nseg + sg;
             unsigned *cur = cnt + tile * kSegWarps + w;
@@ -217,6 +223,10 @@ __global__ void seg_walk_kernel(const int *__restrict__ rowptr, const int *__res
                 scol[pos] = (unsigned short)(c - sg * kSegWidth);
                 srow[pos] = (unsigned short)rl;
             }
+        }
+        if (PASS == 1) {
+            sdiag[r] = dsum;
+            sdiag32[r] = (float)dsum;
         }
     }
 }
@@ -285,6 +295,8 @@ struct perks_op {
     float *sval32 = nullptr;
     unsigned short *scol = nullptr, *srow = nullptr, *swofs = nullptr;
     unsigned *stile_off = nullptr;
+    double *sdiag = nullptr;
+    float *sdiag32 = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
     double *part = nullptr;
@@ -314,7 +326,7 @@ void free_op(perks_op *op) {
     void *ptrs[] = {op->rowptr, op->col, op->val, op->val32, op->part_row, op->part_ntiles,
                     op->part_tiles, op->part_row2, op->part_ntiles2, op->part_tiles2, op->b, op->x, op->r, op->p, op->q, op->r32, op->p32,
                     op->q32, op->d32, op->part, op->trace, op->res, op->ms, op->bar, op->err,
-                    op->sval, op->sval32, op->scol, op->srow, op->swofs, op->stile_off};
+                    op->sval, op->sval32, op->scol, op->srow, op->swofs, op->stile_off, op->sdiag, op->sdiag32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (op->ms_done_host) cudaFreeHost(op->ms_done_host);
@@ -354,6 +366,8 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.seg.row = op->srow;
     a.seg.tile_off = op->stile_off;
     a.seg.wofs = op->swofs;
+    a.seg.diag = op->sdiag;
+    a.seg.diag32 = op->sdiag32;
     a.bar = op->bar;
     a.err = op->err;
     a.timeout_ns = op->ctx->timeout_ns;
@@ -528,7 +542,8 @@ perks_status build_seg(perks_op *op) {
     const int threads = G * kSegWarps;
     if (e == cudaSuccess) {
         seg_walk_kernel<0><<<(threads + 127) / 128, 128>>>(op->rowptr, op->col, op->val, op->part_row, G, nseg, cnt,
-                                                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                           nullptr, nullptr);
         seg_tiles_kernel<<<1, 1024>>>(cnt, ntiles, op->swofs, op->stile_off, total, max_len);
         e = cudaGetLastError();
     }
@@ -543,7 +558,8 @@ perks_status build_seg(perks_op *op) {
     }
     const size_t ne = (size_t)tot + 8;
     if ((rc = dalloc(ctx, &op->sval, ne)) || (rc = dalloc(ctx, &op->sval32, ne)) || (rc = dalloc(ctx, &op->scol, ne)) ||
-        (rc = dalloc(ctx, &op->srow, ne))) {
+        (rc = dalloc(ctx, &op->srow, ne)) || (rc = dalloc(ctx, &op->sdiag, (size_t)op->n)) ||
+        (rc = dalloc(ctx, &op->sdiag32, (size_t)op->n))) {
         cleanup();
         return rc;
     }
@@ -555,7 +571,7 @@ perks_status build_seg(perks_op *op) {
     if (e == cudaSuccess) {
         seg_walk_kernel<1><<<(threads + 127) / 128, 128>>>(op->rowptr, op->col, op->val, op->part_row, G, nseg, cnt,
                                                            op->stile_off, op->swofs, op->sval, op->sval32, op->scol,
-                                                           op->srow);
+                                                           op->srow, op->sdiag, op->sdiag32);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -18,11 +18,12 @@
 // owning warp, then row, then column; per nonzero: the value (fp64, plus an
 // fp32 copy for the fp32 inner solves), the column offset within the segment
 // (u16) and the local row (u16); per tile: its start and the start of each
-// warp's run (kSegWarps + 1 u16, padded to 48 bytes).  Lanes of a warp take
-// consecutive nonzeros; nonzeros of one row that share a 32-wide chunk are
-// applied in lane order, so every row is summed in column order -- the order
-// of a sequential CSR row sum with fused multiply-adds -- whatever the
-// segmentation.
+// warp's run (kSegWarps + 1 u16, padded to 48 bytes).  Diagonal entries stay
+// out of the tiles (a block's own rows would crowd the segments holding its
+// diagonal) and are applied last, per row.  Lanes of a warp take consecutive
+// nonzeros; nonzeros of one row that share a 32-wide chunk are applied in lane
+// order, so every row is summed in column order of its off-diagonal entries,
+// then its diagonal, whatever the segmentation.
 #pragma once
 
 #include "common.cuh"
@@ -45,6 +46,8 @@ struct SegArgs {
     const unsigned short *row;   // row - part_row[g]
     const unsigned *tile_off;    // [G][nseg] first nonzero of the tile (multiple of 8)
     const unsigned short *wofs;  // [G][nseg][kSegOfsPad] warp run starts within the tile, [kSegWarps] = length
+    const double *diag;          // [n] diagonal entries (kept out of the tiles)
+    const float *diag32;
 };
 
 // Shared memory of one segment buffer (sized for fp64) and of the SEG kernel.
@@ -152,6 +155,10 @@ __device__ __forceinline__ void seg_issue(const SegArgs &sg, const V *gval, cons
     bulk_copy_g2s(dst.wofs, sg.wofs + t * kSegOfsPad, bo, bar);
 }
 
+template <typename V> __device__ __forceinline__ const V *seg_diag(const SegArgs &g);
+template <> __device__ __forceinline__ const double *seg_diag<double>(const SegArgs &g) { return g.diag; }
+template <> __device__ __forceinline__ const float *seg_diag<float>(const SegArgs &g) { return g.diag32; }
+
 // vout[r] = sum_j A[r][j] vin[j] for the block's rows; returns the block's
 // share of <dotv, vout> (0 if dotv is null), summed over the block.  `ok` is
 // false if a copy did not complete in time (the error is recorded).
@@ -213,9 +220,10 @@ __device__ double spmv_seg(const SegArgs &sg, int n, int r0, int r1, const V *__
         }
         if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    const V *dg = seg_diag<V>(sg);
     double dot = 0.0;
     for (int i = tid; i < nrows; i += blockDim.x) {
-        const V y = ys[i];
+        const V y = fma(dg[r0 + i], vin[r0 + i], ys[i]);
         vout[r0 + i] = y;
         if (dotv) dot = fma((double)dotv[r0 + i], (double)y, dot);
     }

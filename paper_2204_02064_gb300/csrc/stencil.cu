@@ -3,6 +3,7 @@
 // to the device's SMs and shared memory), launches and the C ABI entry
 // points perks_stencil_*.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -665,6 +666,143 @@ extern "C" perks_status perks_stencil_run(perks_stencil *st, int64_t steps, int3
         rc = read_dev_error(st, s);
         if (rc) return rc;
     }
+    return PERKS_OK;
+}
+
+// ==================================================================== autotuner
+//
+// The tile decomposition that minimises halo traffic (make_plan's model) is
+// not the fastest when a step is bound by the latency of each block's
+// plane-by-plane walk rather than by HBM (small or fully cached domains): a
+// thinner tile along z halves the walk at the price of more halo cells.  The
+// autotuner times a handful of candidate plans on the stencil's own field
+// (restored afterwards) and keeps the fastest: tilings ranked by
+// tz * (1 + halo / volume) plus the model's choice, each with and without the
+// register cache and with 2 or 4 planes per block barrier.
+
+namespace {
+
+struct TileCand {
+    int ntx, nty, ntz;
+    double score;
+};
+
+std::vector<TileCand> tile_candidates(perks_stencil *st, bool per_step, int max_cands) {
+    std::vector<TileCand> all;
+    const int sid = st->shape_id;
+    if (sid < 0) return all;
+    const ShapeInfo &sh = shape_by_id(sid);
+    KernelEntry *kp = find_kernel(st->desc.dtype, sid, false, per_step, st->X, true);
+    if (!kp) return all;
+    const KernelEntry &k = *kp;
+    const int R = sh.radius, RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
+    const int V = k.v;
+    const int X = st->X, Y = st->Y, Z = st->Z, XU = X / V;
+    const int maxG = st->ctx->sm_count;  // one block per SM
+    for (int ntx = 1; ntx <= std::min(XU, 512); ++ntx) {
+        const int txmax = ceil_div(XU, ntx) * V, txmin = (XU / ntx) * V;
+        if (txmin < std::max(RX, 1) || (V > 1 && txmin < 2)) break;
+        if (txmax / V > k.nt) continue;
+        for (int nty = 1; nty <= std::min(Y, 512); ++nty) {
+            const int tymax = ceil_div(Y, nty), tymin = Y / nty;
+            if (tymin < std::max(RY, 1)) break;
+            const long long threads = (long long)(txmax / V) * tymax;
+            if (threads > k.nt || threads * 4 < k.nt) continue;
+            const int ntz = std::min(Z / std::max(RZ, 1), maxG / (ntx * nty));
+            if (ntz < 1 || Z / ntz < std::max(RZ, 1)) continue;
+            if ((long long)ntx * nty * ntz * 4 < 3LL * maxG && ntz < Z / std::max(RZ, 1)) continue;  // idle SMs
+            const int tzmax = ceil_div(Z, ntz);
+            const double halo = 2.0 * RX / txmax + (RY ? 2.0 * RY / tymax : 0.0) + 2.0 * RZ / tzmax;
+            all.push_back({ntx, nty, ntz, tzmax * (1.0 + halo) * (double)k.nt / (double)threads});
+        }
+    }
+    std::sort(all.begin(), all.end(), [](const TileCand &a, const TileCand &b) { return a.score < b.score; });
+    if ((int)all.size() > max_cands) all.resize(max_cands);
+    return all;
+}
+
+}  // namespace
+
+extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t variant, int32_t probe_steps,
+                                               perks_stream stream, perks_stencil_plan *chosen,
+                                               double *ms_per_step) {
+    if (!st) return PERKS_ERR_INVALID_ARG;
+    perks_context *ctx = st->ctx;
+    if (variant != PERKS_PERSISTENT && variant != PERKS_PER_STEP)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_autotune: unknown variant %d", variant);
+    if (probe_steps < 2) return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_autotune: probe_steps >= 2");
+    if (st->shape_id < 0) return fail(ctx, PERKS_ERR_UNSUPPORTED, "stencil_autotune: offsets match no compiled shape");
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool per_step = variant == PERKS_PER_STEP;
+    const long long steps = probe_steps + (probe_steps & 1);  // even: the field buffer index is unchanged
+    // candidate plans: the model's own tiling first, then the latency-ranked ones
+    std::vector<perks_stencil_plan> plans;
+    const bool had_plan = st->has_plan;
+    const perks_stencil_plan saved_plan = st->plan;
+    st->has_plan = false;
+    Plan base;
+    rc = make_plan(st, base, per_step);
+    if (rc) { st->has_plan = had_plan; st->plan = saved_plan; return rc; }
+    std::vector<std::array<int, 3>> tilings = {{base.ntx, base.nty, base.ntz}};
+    for (const TileCand &c : tile_candidates(st, per_step, 6))
+        if (!(c.ntx == base.ntx && c.nty == base.nty && c.ntz == base.ntz)) tilings.push_back({c.ntx, c.nty, c.ntz});
+    for (const auto &t : tilings)
+        for (int reg = per_step ? 0 : 1; reg >= 0; --reg)
+            for (int P : {2, 4}) {
+                perks_stencil_plan p{};
+                p.tiles_x = t[0]; p.tiles_y = t[1]; p.tiles_z = t[2];
+                p.smem_cache_planes = -1;
+                p.reg_cache = reg;
+                p.reserved[1] = P;
+                plans.push_back(p);
+            }
+    // save the field; every trial starts from it
+    void *saved = nullptr;
+    const size_t bytes = (size_t)st->cells * st->es;
+    PERKS_CUDA(ctx, cudaMalloc(&saved, bytes));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e300;
+    perks_stencil_plan best = plans[0];
+    perks_status out = PERKS_OK;
+    cudaError_t ce = cudaMemcpyAsync(saved, st->field[st->cur], bytes, cudaMemcpyDeviceToDevice, s);
+    for (size_t i = 0; i < plans.size() && ce == cudaSuccess && out == PERKS_OK; ++i) {
+        st->plan = plans[i];
+        st->has_plan = true;
+        Plan probe;
+        if (make_plan(st, probe, per_step) != PERKS_OK) continue;  // plan not hostable
+        if (probe.ntx != plans[i].tiles_x || probe.nty != plans[i].tiles_y || probe.ntz != plans[i].tiles_z) continue;
+        ce = cudaMemcpyAsync(st->field[st->cur], saved, bytes, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) break;
+        ce = cudaEventRecord(e0, s);
+        const perks_status r = perks_stencil_run(st, steps, variant, stream, nullptr);
+        if (r == PERKS_ERR_LAUNCH_TOO_LARGE || r == PERKS_ERR_UNSUPPORTED) continue;
+        if (r != PERKS_OK) { out = r; break; }
+        ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) break;
+        const perks_status dev = read_dev_error(st, s);
+        if (dev != PERKS_OK) { out = dev; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / (double)steps;
+        if (per < best_ms) { best_ms = per; best = plans[i]; }
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(st->field[st->cur], saved, bytes, cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(saved);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) { st->plan = saved_plan; st->has_plan = had_plan; return cuda_fail(ctx, ce, "stencil_autotune"); }
+    if (out != PERKS_OK) { st->plan = saved_plan; st->has_plan = had_plan; return out; }
+    if (best_ms >= 1e300) { st->plan = saved_plan; st->has_plan = had_plan; return fail(ctx, PERKS_ERR_UNSUPPORTED, "stencil_autotune: no candidate plan ran"); }
+    st->plan = best;
+    st->has_plan = true;
+    if (chosen) *chosen = best;
+    if (ms_per_step) *ms_per_step = best_ms;
     return PERKS_OK;
 }
 

@@ -114,6 +114,8 @@ enum DutyKind : int { DUTY_NONE = 0, DUTY_BND_VEC, DUTY_BND_PAIR, DUTY_FIELD_VEC
 struct VecPlan {
     int tile, x0, y0, z0, tx, ty, tz;
     bool own;
+    bool shl, shr;      // left / right x-neighbour cells come from lane-1 / lane+1 (same row)
+    unsigned own_mask;  // lanes of this warp that own cells
     int lx0, ly;
     long long gxy;      // field offset of the thread's first cell at z = 0
     int sidx;           // ring index of the thread's first cell
@@ -149,6 +151,9 @@ __device__ __forceinline__ VecPlan make_vec_plan(const PersistentArgs &a, int ti
     const int nvx = p.tx / V;
     const int c = threadIdx.x;
     p.own = c < nvx * p.ty;
+    p.own_mask = __ballot_sync(0xffffffffu, p.own);
+    p.shl = p.own && (c % nvx) > 0 && (c & 31) > 0;
+    p.shr = p.own && (c % nvx) + 1 < nvx && (c & 31) < 31;
     p.lx0 = p.own ? (c % nvx) * V : 0;
     p.ly = p.own ? c / nvx : 0;
     p.gxy = (long long)(p.x0 + p.lx0) + (long long)(p.y0 + p.ly) * a.X;
@@ -316,20 +321,22 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
                 constexpr int j = decltype(JI)::value;
                 seg[r][R + j] = to_acc(c.v[j]);
             });
+            // x-neighbour cells: from the adjacent lanes' vectors of the same
+            // row by warp shuffles; lanes at a row or warp edge read the ring
             if constexpr (left) {
-                T l[R];
-                load_cells<T, R>(rp - R, l);
                 static_for<0, R>([&](auto JI) {
                     constexpr int j = decltype(JI)::value;
-                    seg[r][j] = to_acc(l[j]);
+                    const A v = __shfl_up_sync(tp.own_mask, seg[r][V + j], 1);  // lane-1's cell V-R+j
+                    if (tp.shl) seg[r][j] = v;
+                    else seg[r][j] = to_acc(rp[j - R]);
                 });
             }
             if constexpr (right) {
-                T rr[R];
-                load_cells<T, R>(rp + V, rr);
                 static_for<0, R>([&](auto JI) {
                     constexpr int j = decltype(JI)::value;
-                    seg[r][R + V + j] = to_acc(rr[j]);
+                    const A v = __shfl_down_sync(tp.own_mask, seg[r][R + j], 1);  // lane+1's cell j
+                    if (tp.shr) seg[r][R + V + j] = v;
+                    else seg[r][R + V + j] = to_acc(rp[V + j]);
                 });
             }
         });

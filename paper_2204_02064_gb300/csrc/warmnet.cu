@@ -146,14 +146,66 @@ __global__ void __launch_bounds__(kMaxC * 9) wgrad_kernel(const SX *__restrict__
     if (t < COUT) atomicAdd(db + t, bacc);
 }
 
+// Network input: channel 0 = log k, channel 1 = f, each averaged over the
+// F x F fine cells of a coarse cell (F = 1: the cells themselves).
 template <typename S>
-__global__ void features_kernel(const double *__restrict__ k, const double *__restrict__ f, S *x0, long long plane,
-                                int nimg) {
+__global__ void features_kernel(const double *__restrict__ k, const double *__restrict__ f, S *x0, int ny, int nx,
+                                int F, int nimg) {
+    const int H = ny / F, W = nx / F;
+    const long long plane = (long long)H * W;
+    const double inv = 1.0 / ((double)F * F);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane * nimg;
          i += (long long)gridDim.x * blockDim.x) {
         const long long img = i / plane, p = i % plane;
-        x0[(img * 2 + 0) * plane + p] = st_f<S>((float)log(k[i]));
-        x0[(img * 2 + 1) * plane + p] = st_f<S>((float)f[i]);
+        const int Y = (int)(p / W), X = (int)(p % W);
+        double lk = 0.0, ff = 0.0;
+        for (int dy = 0; dy < F; ++dy)
+            for (int dx = 0; dx < F; ++dx) {
+                const long long c = (img * ny + (long long)Y * F + dy) * nx + (long long)X * F + dx;
+                lk += log(k[c]);
+                ff += f[c];
+            }
+        x0[(img * 2 + 0) * plane + p] = st_f<S>((float)(lk * inv));
+        x0[(img * 2 + 1) * plane + p] = st_f<S>((float)(ff * inv));
+    }
+}
+
+// Mean of u over each F x F block (training target at the network's grid).
+__global__ void pool_kernel(const double *__restrict__ u, double *ut, int ny, int nx, int F, int nimg) {
+    const int H = ny / F, W = nx / F;
+    const long long plane = (long long)H * W;
+    const double inv = 1.0 / ((double)F * F);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane * nimg;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long img = i / plane, p = i % plane;
+        const int Y = (int)(p / W), X = (int)(p % W);
+        double acc = 0.0;
+        for (int dy = 0; dy < F; ++dy)
+            for (int dx = 0; dx < F; ++dx) acc += u[(img * ny + (long long)Y * F + dy) * nx + (long long)X * F + dx];
+        ut[i] = acc * inv;
+    }
+}
+
+// u = scale * bilinear interpolation of the coarse output at the fine cell
+// centres (coarse cell centres at (Y + 1/2) F - 1/2, clamped at the edges).
+__global__ void upsample_kernel(const float *__restrict__ out, float scale, int ny, int nx, int F, int nimg,
+                                double *u) {
+    const int H = ny / F, W = nx / F;
+    const long long total = (long long)nimg * ny * nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long img = i / ((long long)ny * nx), p = i % ((long long)ny * nx);
+        const int y = (int)(p / nx), x = (int)(p % nx);
+        double yc = (y + 0.5) / F - 0.5, xc = (x + 0.5) / F - 0.5;
+        yc = fmin(fmax(yc, 0.0), (double)(H - 1));
+        xc = fmin(fmax(xc, 0.0), (double)(W - 1));
+        const int y0 = (int)yc, x0 = (int)xc;
+        const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
+        const double wy = yc - y0, wx = xc - x0;
+        const float *o = out + img * (long long)H * W;
+        const double v = (1.0 - wy) * ((1.0 - wx) * o[(long long)y0 * W + x0] + wx * o[(long long)y0 * W + x1]) +
+                         wy * ((1.0 - wx) * o[(long long)y1 * W + x0] + wx * o[(long long)y1 * W + x1]);
+        u[i] = v * scale;
     }
 }
 
@@ -232,6 +284,9 @@ struct perks_warmnet {
     int dil[4] = {1, 2, 4, 8};
     int storage = PERKS_BF16;
     float out_scale = 1.f;
+    int pool = 1;                // the network runs on the grid coarsened by this factor
+    double *ut = nullptr;        // pooled training target
+    long long cap_ut = 0;
     int nparams = 0;
     int off_w[4], off_b[4];
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
@@ -269,14 +324,16 @@ perks_status ensure_bufs(perks_warmnet *n, long long pixels) {
     return PERKS_OK;
 }
 
+// Forward pass on nimg fine images of ny x nx cells: features pooled to the
+// network grid H x W = (ny / pool) x (nx / pool), output left in outb.
 template <typename S>
-perks_status forward(perks_warmnet *n, int nimg, int H, int W, const double *k, const double *f, cudaStream_t s) {
+perks_status forward(perks_warmnet *n, int nimg, int ny, int nx, const double *k, const double *f, cudaStream_t s) {
     perks_context *ctx = n->ctx;
-    const long long plane = (long long)H * W;
+    const int H = ny / n->pool, W = nx / n->pool;
     const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     const dim3 grid(tx * ty, nimg);
     S *x0 = (S *)n->x0, *x1 = (S *)n->x1, *x2 = (S *)n->x2, *x3 = (S *)n->x3;
-    features_kernel<S><<<1024, 256, 0, s>>>(k, f, x0, plane, nimg);
+    features_kernel<S><<<1024, 256, 0, s>>>(k, f, x0, ny, nx, n->pool, nimg);
     const float *P = n->params;
     {
         auto kern = conv_kernel<S, S, 2, kMaxC, false, true, false, float>;
@@ -376,16 +433,30 @@ struct Rng {
     }
 };
 
-perks_status loss_and_grad(perks_warmnet *n, int nimg, int H, int W, const double *k, const double *f,
+perks_status loss_and_grad(perks_warmnet *n, int nimg, int ny, int nx, const double *k, const double *f,
                            const double *u, cudaStream_t s) {
     perks_context *ctx = n->ctx;
+    const int H = ny / n->pool, W = nx / n->pool;
     const long long pixels = (long long)nimg * H * W;
     perks_status rc = ensure_bufs(n, pixels);
     if (rc) return rc;
-    rc = n->storage == PERKS_BF16 ? forward<__nv_bfloat16>(n, nimg, H, W, k, f, s) : forward<float>(n, nimg, H, W, k, f, s);
+    const double *target = u;
+    if (n->pool > 1) {
+        if (pixels > n->cap_ut) {
+            if (n->ut) cudaFree(n->ut);
+            n->ut = nullptr;
+            n->cap_ut = 0;
+            PERKS_CUDA(ctx, cudaMalloc(&n->ut, sizeof(double) * pixels));
+            n->cap_ut = pixels;
+        }
+        pool_kernel<<<1024, 256, 0, s>>>(u, n->ut, ny, nx, n->pool, nimg);
+        target = n->ut;
+    }
+    rc = n->storage == PERKS_BF16 ? forward<__nv_bfloat16>(n, nimg, ny, nx, k, f, s)
+                                  : forward<float>(n, nimg, ny, nx, k, f, s);
     if (rc) return rc;
     PERKS_CUDA(ctx, cudaMemsetAsync(n->loss, 0, sizeof(float), s));
-    mse_kernel<<<1024, 256, 0, s>>>(n->outb, u, 1.f / n->out_scale, pixels, n->g1, n->loss);
+    mse_kernel<<<1024, 256, 0, s>>>(n->outb, target, 1.f / n->out_scale, pixels, n->g1, n->loss);
     PERKS_CUDA(ctx, cudaGetLastError());
     return n->storage == PERKS_BF16 ? backward<__nv_bfloat16>(n, nimg, H, W, s) : backward<float>(n, nimg, H, W, s);
 }
@@ -442,7 +513,7 @@ extern "C" perks_status perks_warmnet_destroy(perks_warmnet *n) {
     if (!n) return PERKS_OK;
     if (n->ctx) cudaSetDevice(n->ctx->device);
     free_net_bufs(n);
-    void *p[] = {n->params, n->grads, n->m, n->v, n->loss};
+    void *p[] = {n->params, n->grads, n->m, n->v, n->loss, n->ut};
     for (void *q : p) if (q) cudaFree(q);
     delete n;
     return PERKS_OK;
@@ -474,13 +545,16 @@ extern "C" perks_status perks_warmnet_predict(perks_warmnet *n, int32_t nimg, in
     if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u) return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_predict: bad arguments");
     perks_status rc = use_device(n->ctx);
     if (rc) return rc;
+    if (ny % n->pool || nx % n->pool)
+        return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_predict: grid not divisible by the pool factor %d", n->pool);
     cudaStream_t s = (cudaStream_t)stream;
-    const long long pixels = (long long)nimg * ny * nx;
+    const long long pixels = (long long)nimg * (ny / n->pool) * (nx / n->pool);
     rc = ensure_bufs(n, pixels);
     if (rc) return rc;
     rc = n->storage == PERKS_BF16 ? forward<__nv_bfloat16>(n, nimg, ny, nx, k, f, s) : forward<float>(n, nimg, ny, nx, k, f, s);
     if (rc) return rc;
-    to_u_kernel<<<1024, 256, 0, s>>>(n->outb, n->out_scale, pixels, u);
+    if (n->pool == 1) to_u_kernel<<<1024, 256, 0, s>>>(n->outb, n->out_scale, pixels, u);
+    else upsample_kernel<<<1024, 256, 0, s>>>(n->outb, n->out_scale, ny, nx, n->pool, nimg, u);
     PERKS_CUDA(n->ctx, cudaGetLastError());
     return PERKS_OK;
 }
@@ -489,7 +563,8 @@ extern "C" perks_status perks_warmnet_gradient(perks_warmnet *n, int32_t nimg, i
                                                const double *f, const double *u, float *grad_host, float *loss_host,
                                                perks_stream stream) {
     if (!n) return PERKS_ERR_INVALID_ARG;
-    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u) return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_gradient: bad arguments");
+    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u || ny % n->pool || nx % n->pool)
+        return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_gradient: bad arguments");
     perks_status rc = use_device(n->ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
@@ -505,7 +580,7 @@ extern "C" perks_status perks_warmnet_train_step(perks_warmnet *n, int32_t nimg,
                                                  const double *k, const double *f, const double *u, float lr,
                                                  perks_stream stream, float *loss_host) {
     if (!n) return PERKS_ERR_INVALID_ARG;
-    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u || !(lr > 0.f))
+    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u || !(lr > 0.f) || ny % n->pool || nx % n->pool)
         return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_train_step: bad arguments");
     perks_status rc = use_device(n->ctx);
     if (rc) return rc;
@@ -530,7 +605,8 @@ extern "C" perks_status perks_warmnet_fit(perks_warmnet *n, int32_t nimg, int32_
                                           int32_t auto_scale, uint64_t seed, perks_stream stream, float *epoch_loss) {
     if (!n) return PERKS_ERR_INVALID_ARG;
     perks_context *ctx = n->ctx;
-    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u || batch < 1 || epochs < 0 || !(lr > 0.f))
+    if (nimg < 1 || ny < 1 || nx < 1 || !k || !f || !u || batch < 1 || epochs < 0 || !(lr > 0.f) ||
+        ny % n->pool || nx % n->pool)
         return fail(ctx, PERKS_ERR_INVALID_ARG, "warmnet_fit: bad arguments");
     perks_status rc = use_device(ctx);
     if (rc) return rc;
@@ -579,6 +655,13 @@ extern "C" perks_status perks_warmnet_fit(perks_warmnet *n, int32_t nimg, int32_
         }
         if (epoch_loss) epoch_loss[ep] = (float)(sum / nimg);
     }
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_warmnet_set_pool(perks_warmnet *n, int32_t factor) {
+    if (!n) return PERKS_ERR_INVALID_ARG;
+    if (factor < 1 || factor > 32) return fail(n->ctx, PERKS_ERR_INVALID_ARG, "warmnet_set_pool: factor in 1..32");
+    n->pool = factor;
     return PERKS_OK;
 }
 

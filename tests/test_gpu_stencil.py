@@ -346,3 +346,26 @@ def test_step_trace(ctx, oracle):
     st.get_field(out)
     assert rel_err(out.cpu().numpy(), oracle.stencil_run(f, offs, w, 8)) <= 1e-12
     st.set_trace(0)
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["persistent", "per_step"])
+@pytest.mark.parametrize("name,shape,dtype", [("3d7pt", (40, 48, 64), "f32"), ("2d5pt", (96, 128), "f64")])
+def test_autotune_keeps_field_and_results(ctx, oracle, name, shape, dtype, variant):
+    """The autotuner leaves the field as it found it and the plan it installs
+    gives the oracle's results."""
+    from paper_2204_02064_gb300 import api
+    f = inputs.stencil_field(shape, 37)
+    offs, w = inputs.shape_offsets(name), inputs.workload_weights(name)
+    st = api.Stencil(ctx, shape, offs, w, dtype=dtype)
+    src = torch.from_numpy(f.astype(NP[dtype])).cuda()
+    st.set_field(src)
+    plan = st.autotune(variant, probe_steps=4)
+    assert plan["ms_per_step"] > 0
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, src)
+    st.run(9, variant=variant, stats=True)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    assert rel_err(out.cpu().numpy(), oracle.stencil_run(f, offs, w, 9)) <= TOL[dtype]

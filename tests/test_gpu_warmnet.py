@@ -177,3 +177,66 @@ def test_trained_net_gains_over_zero_start(ctx):
     print("zero-start mean iterations %.1f, warm-start %.1f, losses %s"
           % (zero["mean_iterations"], warm["mean_iterations"], losses[[0, -1]]))
     assert warm["mean_iterations"] < zero["mean_iterations"]
+
+
+def _pool(a, F):
+    n, ny, nx = a.shape
+    return a.reshape(n, ny // F, F, nx // F, F).mean(axis=(2, 4))
+
+
+def _bilinear(c, F):
+    """Cell-centred bilinear interpolation of (n, H, W) to (n, H F, W F), clamped."""
+    n, H, W = c.shape
+    yc = np.clip((np.arange(H * F) + 0.5) / F - 0.5, 0, H - 1)
+    xc = np.clip((np.arange(W * F) + 0.5) / F - 0.5, 0, W - 1)
+    y0 = np.floor(yc).astype(int)
+    x0 = np.floor(xc).astype(int)
+    y1 = np.minimum(y0 + 1, H - 1)
+    x1 = np.minimum(x0 + 1, W - 1)
+    wy = (yc - y0)[:, None]
+    wx = (xc - x0)[None, :]
+    out = np.empty((n, H * F, W * F))
+    for i in range(n):
+        o = c[i]
+        out[i] = (1 - wy) * ((1 - wx) * o[y0][:, x0] + wx * o[y0][:, x1]) + wy * ((1 - wx) * o[y1][:, x0] + wx * o[y1][:, x1])
+    return out
+
+
+@pytest.mark.parametrize("F", [2, 4])
+def test_pooled_forward_matches_oracle(ctx, oracle, F):
+    """Coarse-grid mode: inputs averaged over F x F blocks, the network on the
+    coarse grid, the output interpolated bilinearly back to the fine cells."""
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = 2, 32, 40
+    k, f = _case(nimg, ny, nx, 51)
+    net = api.WarmNet(ctx, storage=api.F32, dilations=DIL, seed=1, pool=F)
+    p = _params(7)
+    net.params = p
+    net.scale = 3.0
+    u = torch.zeros((nimg, ny, nx), dtype=torch.float64, device="cuda")
+    net.predict(_dev(k), _dev(f), u)
+    torch.cuda.synchronize()
+    x = np.stack([_pool(np.log(k), F), _pool(f, F)], axis=1).astype(np.float32).astype(np.float64)
+    coarse = np.stack([oracle.warmnet_forward(p.astype(np.float64), x[i], C1, DIL) for i in range(nimg)])
+    ref = _bilinear(coarse, F) * 3.0
+    got = u.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    with pytest.raises(api.PerksError):
+        net.predict(_dev(k[:, :31, :]), _dev(f[:, :31, :]), torch.zeros((nimg, 31, nx), dtype=torch.float64,
+                                                                       device="cuda"))
+
+
+def test_pooled_gradient_matches_oracle(ctx, oracle):
+    from paper_2204_02064_gb300 import api
+    F, nimg, ny, nx = 2, 2, 24, 30
+    k, f = _case(nimg, ny, nx, 52)
+    u = inputs.uniform(53, nimg * ny * nx).reshape(nimg, ny, nx) * 2.0 - 1.0
+    net = api.WarmNet(ctx, storage=api.F32, dilations=DIL, seed=1, pool=F)
+    p = _params(8)
+    net.params = p
+    net.scale = 0.5
+    loss, g = net.gradient(_dev(k), _dev(f), _dev(u))
+    x = np.stack([_pool(np.log(k), F), _pool(f, F)], axis=1).astype(np.float32).astype(np.float64)
+    ref_loss, ref_g = oracle.warmnet_grad(p.astype(np.float64), x, _pool(u, F) / 0.5, C1, DIL)
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
