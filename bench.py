@@ -290,8 +290,8 @@ def batch_leg(api, torch, ctx, K):
     return out
 
 
-def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, batch=16, lr=1e-3,
-                  label_rtol=1e-6, max_iter=100000):
+def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=8, batch=16, lr=1e-3,
+                  label_rtol=1e-6, max_iter=100000, pool=4):
     """The variable-coefficient Poisson workload: 256 problems on 512^2
     grids, k = exp(GRF, length 32, sigma 1), f uniform[-1,1), Dirichlet 0;
     CG to 1e-8 from zero vs from the BF16 warm-start network (inference
@@ -300,7 +300,7 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, bat
     from paper_2204_02064_gb300 import inputs
     stream = torch.cuda.current_stream()
     out = {"n": n, "problems": nprob, "rtol": 1e-8, "train_pairs": ntrain, "epochs": epochs, "batch": batch,
-           "label_rtol": label_rtol}
+           "label_rtol": label_rtol, "pool": pool}
     # training pairs, generated and solved in chunks of nprob problems
     t0 = time.perf_counter()
     ks, fs, us = [], [], []
@@ -323,7 +323,7 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, bat
     torch.cuda.synchronize()
     out["generate_s"] = time.perf_counter() - t0
     out["generate_mean_iterations"] = float(np.mean(chunk_iters))
-    net = api.WarmNet(ctx, storage=api.BF16, seed=7)
+    net = api.WarmNet(ctx, storage=api.BF16, seed=7, pool=pool)
     t0 = time.perf_counter()
     losses = net.fit(k_tr, f_tr, u_tr, batch=batch, epochs=epochs, lr=lr)
     torch.cuda.synchronize()
@@ -337,29 +337,34 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=4, bat
     P = api.Poisson(ctx, k)
     x = torch.zeros_like(f)
     u0 = torch.zeros_like(f)
-    res = {}
+    res = {"zero": {"ms_runs": []}, "warm": {"ms_runs": [], "inference_ms": []}}
+    for rep in range(2):  # alternate the two starts, twice
+        for name in ("zero", "warm") if rep == 0 else ("warm", "zero"):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            ei = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "warm":
+                net.predict(k, f, x)
+            ei.record(stream)
+            P.solve(f, x, rtol=1e-8, max_iter=max_iter, stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            res[name]["ms_runs"].append(e0.elapsed_time(e1))
+            if name == "warm":
+                res[name]["inference_ms"].append(e0.elapsed_time(ei))
     for name in ("zero", "warm"):
-        x.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        ei = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if name == "warm":
-            net.predict(k, f, x)
-        ei.record(stream)
-        P.solve(f, x, rtol=1e-8, max_iter=max_iter, stats=False)
-        e1.record(stream)
-        e1.synchronize()
-        ms, ms_inf = e0.elapsed_time(e1), e0.elapsed_time(ei)
         # the same solve again for the per-problem statistics (untimed)
         x.zero_()
         if name == "warm":
             net.predict(k, f, x)
         stats = P.solve(f, x, rtol=1e-8, max_iter=max_iter)
-        res[name] = {"ms_to_tol": ms, "inference_ms": ms_inf if name == "warm" else 0.0,
-                     "mean_iterations": stats["mean_iterations"], "max_iterations": stats["max_iterations"],
-                     "max_true_rel_residual": stats["max_true_rel_residual"]}
+        res[name].update({"ms_to_tol": min(res[name]["ms_runs"]), "mean_iterations": stats["mean_iterations"],
+                          "max_iterations": stats["max_iterations"],
+                          "max_true_rel_residual": stats["max_true_rel_residual"]})
+    res["warm"]["inference_ms"] = min(res["warm"]["inference_ms"])
     out.update(res)
     out["speedup"] = res["zero"]["ms_to_tol"] / res["warm"]["ms_to_tol"]
     P.close()
@@ -434,14 +439,16 @@ def main():
                     help="run one extra workload and print its JSON (warmstart: the learned "
                          "warm start for the 512^2 x 256 Poisson problems)")
     ap.add_argument("--ws-train", type=int, default=10000, help="warm start: training pairs")
-    ap.add_argument("--ws-epochs", type=int, default=4, help="warm start: training epochs")
+    ap.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
+    ap.add_argument("--ws-pool", type=int, default=4, help="warm start: network grid coarsening factor")
     args = ap.parse_args()
     if args.leg == "warmstart":
         import torch
         from paper_2204_02064_gb300 import api
         ctx = api.Context(0)
         print(json.dumps({"leg": "warmstart", **warmstart_leg(api, torch, ctx, ntrain=args.ws_train,
-                                                                epochs=args.ws_epochs)}), flush=True)
+                                                                epochs=args.ws_epochs, pool=args.ws_pool)}),
+              flush=True)
         return 0
     if args.profile:
         return profile_case(args.profile)

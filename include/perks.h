@@ -159,8 +159,8 @@ perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t 
 /* Autotuner (not in the paper): times candidate plans for `variant` on the
  * stencil's current field for `probe_steps` (>= 2) steps each -- the model's
  * own tiling and up to six tilings ranked by tz * (1 + halo fraction), each
- * with and without the register cache and with 2 or 4 planes per block
- * barrier -- restores the field, installs the fastest plan (as
+ * with registers + shared memory, shared memory only or no cache, and with 2
+ * or 4 planes per block barrier -- restores the field, installs the fastest plan (as
  * perks_stencil_set_plan would) and returns it with its time per step.
  * Synchronizes `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY,
  * CUDA, BARRIER_TIMEOUT. */

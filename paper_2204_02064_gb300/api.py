@@ -343,7 +343,8 @@ class Stencil:
         self.ctx.check(self._lib.perks_stencil_autotune(self.handle, int(variant), int(probe_steps),
                                                         _stream(stream), ctypes.byref(p), ctypes.byref(ms)))
         return {"tiles": (p.tiles_x, p.tiles_y, p.tiles_z), "reg_cache": p.reg_cache,
-                "planes_per_barrier": p.reserved[1], "ms_per_step": ms.value}
+                "smem_cache_planes": p.smem_cache_planes, "planes_per_barrier": p.reserved[1],
+                "ms_per_step": ms.value}
 
     def set_trace(self, steps: int):
         """Record per-block start/end times of the first ``steps`` steps of the

@@ -677,8 +677,10 @@ extern "C" perks_status perks_stencil_run(perks_stencil *st, int64_t steps, int3
 // thinner tile along z halves the walk at the price of more halo cells.  The
 // autotuner times a handful of candidate plans on the stencil's own field
 // (restored afterwards) and keeps the fastest: tilings ranked by
-// tz * (1 + halo / volume) plus the model's choice, each with and without the
-// register cache and with 2 or 4 planes per block barrier.
+// tz * (1 + halo / volume) plus the model's choice, each with registers +
+// shared memory, shared memory only or no cache (where the FP64 pipe, not HBM,
+// bounds a step, caching only adds work), and with 2 or 4 planes per block
+// barrier.
 
 namespace {
 
@@ -749,12 +751,12 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
     for (const TileCand &c : tile_candidates(st, per_step, 6))
         if (!(c.ntx == base.ntx && c.nty == base.nty && c.ntz == base.ntz)) tilings.push_back({c.ntx, c.nty, c.ntz});
     for (const auto &t : tilings)
-        for (int reg = per_step ? 0 : 1; reg >= 0; --reg)
+        for (int cache = per_step ? 0 : 2; cache >= 0; --cache)  // 2: registers + smem, 1: smem, 0: none
             for (int P : {2, 4}) {
                 perks_stencil_plan p{};
                 p.tiles_x = t[0]; p.tiles_y = t[1]; p.tiles_z = t[2];
-                p.smem_cache_planes = -1;
-                p.reg_cache = reg;
+                p.smem_cache_planes = cache == 0 ? 0 : -1;
+                p.reg_cache = cache == 2 ? 1 : 0;
                 p.reserved[1] = P;
                 plans.push_back(p);
             }
