@@ -421,6 +421,10 @@ perks_status perks_warmnet_set_params(perks_warmnet *net, const float *host);
  * bilinear interpolation of its output at the fine cell centres; grids must
  * then be divisible by the factor (else INVALID_ARG). */
 perks_status perks_warmnet_set_pool(perks_warmnet *net, int32_t factor);
+/* BF16 storage only: run the two 32 -> 32 layers of the forward pass as
+ * implicit GEMMs on the tensor cores (tcgen05.mma, fp32 accumulation in
+ * tensor memory; default) or on the CUDA cores (enable = 0). */
+perks_status perks_warmnet_set_tensor_cores(perks_warmnet *net, int32_t enable);
 /* Output scale (> 0): the network predicts u / scale. */
 perks_status perks_warmnet_set_scale(perks_warmnet *net, float scale);
 float perks_warmnet_get_scale(const perks_warmnet *net);

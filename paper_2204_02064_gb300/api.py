@@ -140,6 +140,7 @@ def _declare(lib):
         "perks_warmnet_set_scale": ([P, ctypes.c_float], i32),
         "perks_warmnet_get_scale": ([P], ctypes.c_float),
         "perks_warmnet_set_pool": ([P, i32], i32),
+        "perks_warmnet_set_tensor_cores": ([P, i32], i32),
         "perks_warmnet_predict": ([P, i32, i32, i32, P, P, P, P], i32),
         "perks_warmnet_gradient": ([P, i32, i32, i32, P, P, P, P, P, P], i32),
         "perks_warmnet_train_step": ([P, i32, i32, i32, P, P, P, ctypes.c_float, P, P], i32),
@@ -632,6 +633,10 @@ class WarmNet:
         self.pool = int(pool)
         if self.pool != 1:
             ctx.check(self._lib.perks_warmnet_set_pool(h, self.pool))
+
+    def set_tensor_cores(self, enable: bool):
+        """BF16 storage: inner layers on the tensor cores (default) or CUDA cores."""
+        self.ctx.check(self._lib.perks_warmnet_set_tensor_cores(self.handle, int(bool(enable))))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -387,6 +387,7 @@ void fill_args(const perks_stencil *st, const Plan &pl, long long steps, Persist
     a.boundary_f = (float)st->desc.boundary;
     for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
     a.face_plane = (long long)pl.tzmax * pl.tymax;
+    a.faces_cached_only = 1;
 }
 
 perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, Plan &pl) {

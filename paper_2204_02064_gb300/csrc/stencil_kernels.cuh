@@ -89,6 +89,10 @@ struct PersistentArgs {
     // trace[((k + 1) * gridDim.x + block) * 2 + {0, 1}], for k < trace_steps
     unsigned long long *trace;
     int trace_steps;
+    // 1: x-edges go through the face buffers only for cached planes (the
+    // field holds every uncached plane, so neighbours read its x-halo there);
+    // requires every tile of a z-layer to cache the same planes
+    int faces_cached_only;
 };
 
 __device__ __forceinline__ void trace_mark(const PersistentArgs &a, long long k, int which) {

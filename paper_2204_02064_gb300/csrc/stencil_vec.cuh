@@ -286,7 +286,7 @@ __device__ __forceinline__ void vfill_fast(const PersistentArgs &a, const VecPla
             else { PT x; x.v[0] = bnd; x.v[1] = bnd; *reinterpret_cast<PT *>(d) = x; }
         } else if (tp.duty == DUTY_FIELD_VEC) {
             copy_vec<T, V>(d, sp.fill_duty);
-        } else if (tp.duty == DUTY_XPAIR && inside && !PER_STEP) {
+        } else if (tp.duty == DUTY_XPAIR && inside && !PER_STEP && (FILL != PC_GLOBAL || !a.faces_cached_only)) {
             cp_async<sizeof(T) * 2>(d, sp.face_src);
         } else {
             cp_async<sizeof(T) * 2>(d, sp.fill_duty);
@@ -363,7 +363,7 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
             to_field = true;
         }
         if (to_field) *reinterpret_cast<VT *>(sp.store_own) = out;
-        if (!PER_STEP) {
+        if (!PER_STEP && (STORE != PC_GLOBAL || !a.faces_cached_only)) {
             if (tp.wface) {
                 PT x; x.v[0] = out.v[0]; x.v[1] = out.v[V >= 2 ? 1 : 0];
                 *reinterpret_cast<PT *>(sp.face_dst_w) = x;

@@ -13,10 +13,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "internal.h"
+#include "warmnet_tc.cuh"
 
 using namespace perks;
 
@@ -285,6 +287,8 @@ struct perks_warmnet {
     int storage = PERKS_BF16;
     float out_scale = 1.f;
     int pool = 1;                // the network runs on the grid coarsened by this factor
+    bool tensor_cores = true;    // bf16 storage: inner layers on tcgen05 (else CUDA cores)
+    DevError *err = nullptr;
     double *ut = nullptr;        // pooled training target
     long long cap_ut = 0;
     int nparams = 0;
@@ -343,7 +347,17 @@ perks_status forward(perks_warmnet *n, int nimg, int ny, int nx, const double *k
         kern<<<grid, kConvThreads, sm, s>>>(x0, P + n->off_w[0], P + n->off_b[0], x1, (const float *)nullptr, H, W,
                                            n->dil[0], tx, ty);
     }
-    {
+    if (std::is_same<S, __nv_bfloat16>::value && n->tensor_cores) {
+        // inner layers as implicit GEMMs on the tensor cores
+        perks_status rc = set_smem(ctx, tc_conv32_kernel, tc_conv_smem());
+        if (rc) return rc;
+        const long long ntiles = (long long)nimg * H * ((W + kTcPix - 1) / kTcPix);
+        const int blocks = (int)std::min<long long>(ntiles, 2LL * ctx->sm_count);
+        for (int l = 1; l <= 2; ++l)
+            tc_conv32_kernel<<<blocks, kTcThreads, tc_conv_smem(), s>>>(
+                reinterpret_cast<const __nv_bfloat16 *>(l == 1 ? x1 : x2), P + n->off_w[l], P + n->off_b[l],
+                reinterpret_cast<__nv_bfloat16 *>(l == 1 ? x2 : x3), nimg, H, W, n->dil[l], n->err);
+    } else {
         auto kern = conv_kernel<S, S, kMaxC, kMaxC, false, true, false, float>;
         for (int l = 1; l <= 2; ++l) {
             const size_t sm = conv_smem(kMaxC, kMaxC, n->dil[l]);
@@ -501,6 +515,8 @@ extern "C" perks_status perks_warmnet_create(perks_context *ctx, const int32_t *
     if (e == cudaSuccess) e = cudaMalloc(&n->m, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMalloc(&n->v, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(DevError));
+    if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(DevError));
     if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(n->v, 0, sizeof(float) * o);
@@ -513,7 +529,7 @@ extern "C" perks_status perks_warmnet_destroy(perks_warmnet *n) {
     if (!n) return PERKS_OK;
     if (n->ctx) cudaSetDevice(n->ctx->device);
     free_net_bufs(n);
-    void *p[] = {n->params, n->grads, n->m, n->v, n->loss, n->ut};
+    void *p[] = {n->params, n->grads, n->m, n->v, n->loss, n->ut, n->err};
     for (void *q : p) if (q) cudaFree(q);
     delete n;
     return PERKS_OK;
@@ -571,6 +587,11 @@ extern "C" perks_status perks_warmnet_gradient(perks_warmnet *n, int32_t nimg, i
     rc = loss_and_grad(n, nimg, ny, nx, k, f, u, s);
     if (rc) return rc;
     PERKS_CUDA(n->ctx, cudaStreamSynchronize(s));
+    {
+        DevError de{};
+        PERKS_CUDA(n->ctx, cudaMemcpy(&de, n->err, sizeof(de), cudaMemcpyDeviceToHost));
+        if (de.code) return fail(n->ctx, de.code, "warmnet: a tensor-core wait timed out (block %d)", de.block);
+    }
     if (grad_host) PERKS_CUDA(n->ctx, cudaMemcpy(grad_host, n->grads, sizeof(float) * n->nparams, cudaMemcpyDeviceToHost));
     if (loss_host) PERKS_CUDA(n->ctx, cudaMemcpy(loss_host, n->loss, sizeof(float), cudaMemcpyDeviceToHost));
     return PERKS_OK;
@@ -655,6 +676,12 @@ extern "C" perks_status perks_warmnet_fit(perks_warmnet *n, int32_t nimg, int32_
         }
         if (epoch_loss) epoch_loss[ep] = (float)(sum / nimg);
     }
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_warmnet_set_tensor_cores(perks_warmnet *n, int32_t enable) {
+    if (!n) return PERKS_ERR_INVALID_ARG;
+    n->tensor_cores = enable != 0;
     return PERKS_OK;
 }
 

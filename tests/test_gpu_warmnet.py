@@ -240,3 +240,27 @@ def test_pooled_gradient_matches_oracle(ctx, oracle):
     ref_loss, ref_g = oracle.warmnet_grad(p.astype(np.float64), x, _pool(u, F) / 0.5, C1, DIL)
     assert loss == pytest.approx(ref_loss, rel=1e-4)
     assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
+
+
+@pytest.mark.parametrize("shape", [(2, 7, 300), (1, 33, 128), (3, 16, 40)])
+def test_tensor_core_layers_match_cuda_core_layers(ctx, oracle, shape):
+    """BF16 storage: the inner layers as tcgen05 implicit GEMMs agree with the
+    same layers on the CUDA cores and with the bf16-rounded oracle (ragged
+    128-pixel tiles included)."""
+    from paper_2204_02064_gb300 import api
+    nimg, ny, nx = shape
+    k, f = _case(nimg, ny, nx, 61)
+    p = _params(9)
+    outs = []
+    for tc in (True, False):
+        net = api.WarmNet(ctx, storage=api.BF16, dilations=DIL, seed=1)
+        net.set_tensor_cores(tc)
+        net.params = p
+        u = torch.zeros((nimg, ny, nx), dtype=torch.float64, device="cuda")
+        net.predict(_dev(k), _dev(f), u)
+        torch.cuda.synchronize()
+        outs.append(u.cpu().numpy())
+        net.close()
+    scale = np.max(np.abs(outs[1]))
+    assert np.max(np.abs(outs[0] - outs[1])) <= 1e-2 * scale
+    assert np.corrcoef(outs[0].ravel(), outs[1].ravel())[0, 1] > 0.9999
