@@ -589,7 +589,8 @@ def main():
                          "frac": tflops / fp64_peak, "traffic": traffic,
                          "peak_kind": "derived: 152 SMs x 2 fp64 FMA/clk x 2 FLOP x max SM clock "
                                       f"{sm_mhz:.0f} MHz",
-                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, V=2, ZR=8, D=8>",
+                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, NT=512, V=2, ZR=%d, D=8, P=%d>"
+                                   % (8 if tuned["reg_cache"] else 0, tuned["planes_per_barrier"]),
                          "flop_per_cell_update": flop_per_cell,
                          "algorithmic_bytes_per_launch": desc["algorithmic_bytes"],
                          "mean_launch_ms": mean_launch_ms,
@@ -625,11 +626,17 @@ def profile_case(name):
         f = torch.from_numpy(inputs.stencil_field(shape, 1)).cuda()
         st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
         st.set_field(f)
-        st.run(2, stats=True)                      # warm-up launch (not captured: -s 1)
+        tuned = st.autotune(api.PERSISTENT, probe_steps=10)   # the bench's own plan choice
+        st.set_field(f)
+        st.run(2, stats=True)                      # warm-up launch
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("capture")      # ncu --nvtx --nvtx-include capture/ selects these
         for steps in (20, 40):
             st.set_field(f)
             d = st.run(steps, stats=True)
-            print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d}))
+            print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d, "tuned": tuned}))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     elif name.startswith("stencil3d") or name.startswith("stencil384"):
         dt = "f64" if "f64" in name else ("bf16" if "bf16" in name else "f32")
         variant = api.PER_STEP if name.endswith("perstep") else api.PERSISTENT
