@@ -647,6 +647,10 @@ def profile_case(name):
             {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]).cuda()
         st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"),
                          dtype=dt)
+        plan = os.environ.get("PERKS_PROFILE_PLAN")  # "tx,ty,tz,reg_cache,smem_planes,planes_per_barrier"
+        if plan:
+            tx, ty, tz, reg, zs, P = (int(v) for v in plan.split(","))
+            st.set_plan(tiles=(tx, ty, tz), reg_cache=reg, smem_cache_planes=zs, planes_per_barrier=P)
         for _ in range(2):
             st.set_field(f)
             d = st.run(steps, variant, stats=True)
