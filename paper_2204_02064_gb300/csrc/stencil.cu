@@ -203,9 +203,18 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
         allow_vec = st->plan.reserved[0] == 0;  // reserved[0] = 1 forces the scalar kernel
         want_p = st->plan.reserved[1];          // planes per barrier (0 = automatic)
     }
-    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec, want_p);
+    // A persistent plan that caches nothing runs the cache-free kernel body
+    // (the per-step one) for all steps in one cooperative launch, with the
+    // grid barrier between steps: the launch overhead goes, nothing is added
+    // per plane.
+    const bool body_per_step = per_step || (st->has_plan && st->plan.reg_cache == 0 &&
+                                            st->plan.smem_cache_planes == 0 && allow_vec);
+    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, want_p);
     if (!kp && want_p > 0)
-        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, per_step, st->X, allow_vec, 0);
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, 0);
+    if (!kp && body_per_step && !per_step)  // no vectorised cache-free body for this extent
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, false, st->X, allow_vec, want_p);
+    per_step = per_step || (kp && kp->per_step);
     if (!kp)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "no %s kernel for this dtype/shape/extent (bf16 needs nx divisible by 8)",
