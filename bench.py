@@ -589,8 +589,10 @@ def main():
                          "frac": tflops / fp64_peak, "traffic": traffic,
                          "peak_kind": "derived: 152 SMs x 2 fp64 FMA/clk x 2 FLOP x max SM clock "
                                       f"{sm_mhz:.0f} MHz",
-                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, NT=512, V=2, ZR=%d, D=8, P=%d>"
-                                   % (8 if tuned["reg_cache"] else 0, tuned["planes_per_barrier"]),
+                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, NT=512, V=2, ZR=%d, D=8, %s, P=%d>"
+                                   % (8 if tuned["reg_cache"] else 0,
+                                      "cache-free body" if not tuned["reg_cache"] and tuned["smem_cache_planes"] == 0
+                                      else "cached body", tuned["planes_per_barrier"]),
                          "flop_per_cell_update": flop_per_cell,
                          "algorithmic_bytes_per_launch": desc["algorithmic_bytes"],
                          "mean_launch_ms": mean_launch_ms,
