@@ -339,7 +339,8 @@ typedef struct {
  * doubles) holds x0 on entry and the solution on exit; both are device
  * pointers when on_device = 1, host pointers otherwise.  `max_iter` bounds
  * the recurrence iterations; for FP32_IR `inner_rtol` is the inner solves'
- * relative tolerance (ignored otherwise).  On exit the true residual is
+ * relative tolerance, 0 = automatic: sqrt(rtol) clamped to [1e-6, 0.1], so
+ * that two refinement steps reach rtol (ignored for the other modes).  On exit the true residual is
  * recomputed in fp64; above tolerance the solver restarts (FP64) or refines
  * again (FP32_IR) while iterations remain.  With stats == NULL the call is
  * asynchronous and returns 0 once launched; the outcome is then read by

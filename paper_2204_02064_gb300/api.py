@@ -453,7 +453,7 @@ class CsrOperator:
         self.ctx.check(self._lib.perks_csr_spmv(self.handle, xp, yp, _stream(stream)))
 
     def solve(self, b, x, rtol: float = 1e-10, max_iter: int = 10000, mode: int = CG_FP64,
-              inner_rtol: float = 1e-4, stream=None, stats: bool = True, trace_len: int = 0,
+              inner_rtol: float = 0.0, stream=None, stats: bool = True, trace_len: int = 0,
               raise_on_error: bool = True):
         bp, bd, _ = _buffer(b)
         xp, xd, _ = _buffer(x)

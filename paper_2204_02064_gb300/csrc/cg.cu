@@ -2,6 +2,7 @@
 // value copy, the merge-path partition computed once), the persistent solve,
 // the multi-launch baseline and the C ABI entry points perks_csr_* / perks_cg_*.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -735,8 +736,13 @@ extern "C" perks_status perks_cg_solve(perks_op *op, const double *b, double *x,
     if (!(rtol >= 0.0) || max_iter < 0) return fail(ctx, PERKS_ERR_INVALID_ARG, "cg_solve: bad rtol/max_iter");
     if (mode != PERKS_CG_FP64 && mode != PERKS_CG_FP32_IR && mode != PERKS_CG_FP64_MULTI)
         return fail(ctx, PERKS_ERR_INVALID_ARG, "cg_solve: unknown mode %d", mode);
-    if (mode == PERKS_CG_FP32_IR && !(inner_rtol > 0.0 && inner_rtol < 1.0))
-        return fail(ctx, PERKS_ERR_INVALID_ARG, "cg_solve: inner_rtol must be in (0, 1)");
+    if (mode == PERKS_CG_FP32_IR && !(inner_rtol >= 0.0 && inner_rtol < 1.0))
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "cg_solve: inner_rtol must be in [0, 1)");
+    if (mode == PERKS_CG_FP32_IR && inner_rtol == 0.0) {
+        // automatic: two refinement steps of sqrt(rtol) each reach rtol;
+        // fp32 inner solves stall near 1e-6, so no tighter than that
+        inner_rtol = std::min(0.1, std::max(1e-6, std::sqrt(rtol)));
+    }
     perks_status rc = use_device(ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;

@@ -237,3 +237,14 @@ def test_seg_spmv_limits_reported(ctx):
     op.spmv(_dev(np.ones(n)), y)
     torch.cuda.synchronize()
     assert y[1].item() == 2500.0
+
+
+@pytest.mark.parametrize("rtol", [1e-8, 1e-10])
+def test_fp32_ir_automatic_inner_tolerance(ctx, system_full, rtol):
+    """inner_rtol = 0 picks sqrt(rtol): two refinement steps reach the
+    tolerance (the true residual is recomputed in fp64 on the GPU)."""
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_full
+    x, res = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, rtol=rtol, inner_rtol=0.0)
+    assert res["true_rel_residual"] <= rtol
+    assert res["outer_iterations"] <= 3
