@@ -562,6 +562,11 @@ def main():
             variants["batch64"] = batch_leg(api, torch, ctx, 2)
         except Exception as e:
             variants["batch64"] = {"error": str(e)}
+        try:
+            variants["grid_barrier_us"] = {str(b): ctx.barrier_benchmark(b, 512, 2000)
+                                           for b in (info["sm_count"] // 4, info["sm_count"], 2 * info["sm_count"])}
+        except Exception as e:
+            variants["grid_barrier_us"] = {"error": str(e)}
 
     e2e_ms, h2d, d2h = e2e_leg(api, torch, ctx, L_3D, STEPS_3D, max(1, min(args.steps, 3)), 1)
     e2e_ms = _max_over_ranks(world, e2e_ms)

@@ -85,6 +85,14 @@ const char *perks_last_error(const perks_context *ctx);
  * error path).  Errors: INVALID_ARG (ctx NULL or limit < 0). */
 perks_status perks_context_set_barrier_timeout(perks_context *ctx, int64_t limit_ns);
 
+/* Grid-synchronisation cost (a measurement aid): times one cooperative
+ * launch of `blocks` x `threads` that runs `iterations` of the persistent
+ * kernels' grid barrier and nothing else (after one warm-up launch), and
+ * returns the mean microseconds per barrier.  Errors: INVALID_ARG,
+ * LAUNCH_TOO_LARGE (blocks not co-resident), BARRIER_TIMEOUT, CUDA. */
+perks_status perks_barrier_benchmark(perks_context *ctx, int32_t blocks, int32_t threads,
+                                     int32_t iterations, double *us_per_barrier);
+
 /* Device facts used by planners and reports: SM count, opt-in shared memory
  * per block (bytes), L2 size (bytes).  Any out pointer may be NULL. */
 perks_status perks_context_info(const perks_context *ctx, int32_t *sm_count,

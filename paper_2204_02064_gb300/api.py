@@ -107,6 +107,7 @@ def _declare(lib):
         "perks_context_destroy": ([P], i32),
         "perks_last_error": ([P], ctypes.c_char_p),
         "perks_context_set_barrier_timeout": ([P, i64], i32),
+        "perks_barrier_benchmark": ([P, i32, i32, i32, ctypes.POINTER(f64)], i32),
         "perks_context_info": ([P, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(i64)], i32),
         "perks_stencil_create": ([P, ctypes.POINTER(StencilDesc), ctypes.POINTER(P)], i32),
@@ -226,6 +227,13 @@ class Context:
     @property
     def last_error(self) -> str:
         return self._lib.perks_last_error(self.handle).decode()
+
+    def barrier_benchmark(self, blocks: int, threads: int = 512, iterations: int = 2000) -> float:
+        """Microseconds per grid barrier of a `blocks` x `threads` persistent grid."""
+        us = ctypes.c_double()
+        self.check(self._lib.perks_barrier_benchmark(self.handle, int(blocks), int(threads), int(iterations),
+                                                     ctypes.byref(us)))
+        return us.value
 
     def set_barrier_timeout(self, ns: int):
         self.check(self._lib.perks_context_set_barrier_timeout(self.handle, int(ns)))

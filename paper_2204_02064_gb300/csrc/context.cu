@@ -1,8 +1,21 @@
 // Context entry points of the C ABI: device queries, error messages and the
 // barrier time limit shared by every persistent launch.
+#include "common.cuh"
 #include "internal.h"
 
 using namespace perks;
+
+namespace {
+
+// `iterations` grid barriers and nothing else: the per-step synchronisation
+// cost of a persistent kernel with this grid.
+__global__ void barrier_bench_kernel(unsigned long long *counter, DevError *err, int iterations, long long timeout_ns) {
+    unsigned long long epoch = 0;
+    for (int i = 0; i < iterations; ++i)
+        if (!grid_barrier(counter, gridDim.x, epoch, err, timeout_ns)) return;
+}
+
+}  // namespace
 
 extern "C" perks_status perks_context_create(int device, perks_context **out) {
     if (!out) return PERKS_ERR_INVALID_ARG;
@@ -54,5 +67,48 @@ extern "C" perks_status perks_context_info(const perks_context *ctx, int32_t *sm
     if (sm_count) *sm_count = ctx->sm_count;
     if (smem_per_block) *smem_per_block = ctx->smem_optin;
     if (l2_bytes) *l2_bytes = ctx->l2_bytes;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_barrier_benchmark(perks_context *ctx, int32_t blocks, int32_t threads,
+                                                int32_t iterations, double *us_per_barrier) {
+    if (!ctx) return PERKS_ERR_INVALID_ARG;
+    if (blocks < 1 || threads < 32 || threads > 1024 || iterations < 1 || !us_per_barrier)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "barrier_benchmark: bad arguments");
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_bench_kernel, threads, 0));
+    if ((long long)per_sm * ctx->sm_count < blocks)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "barrier_benchmark: %d blocks are not co-resident", blocks);
+    unsigned long long *counter = nullptr;
+    DevError *err = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&counter, sizeof(*counter));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(*err));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    DevError h{};
+    long long tmo = ctx->timeout_ns;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+        e = cudaMemset(counter, 0, sizeof(*counter));
+        if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(*err));
+        void *args[] = {&counter, &err, &iterations, &tmo};
+        if (e == cudaSuccess) e = cudaEventRecord(e0);
+        if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void *)barrier_bench_kernel, dim3(blocks),
+                                                             dim3(threads), args, 0, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(h), cudaMemcpyDeviceToHost);
+    }
+    if (counter) cudaFree(counter);
+    if (err) cudaFree(err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "barrier_benchmark");
+    if (h.code) return fail(ctx, h.code, "barrier_benchmark: barrier wait timed out");
+    *us_per_barrier = 1e3 * ms / iterations;
     return PERKS_OK;
 }

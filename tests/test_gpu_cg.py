@@ -248,3 +248,15 @@ def test_fp32_ir_automatic_inner_tolerance(ctx, system_full, rtol):
     x, res = _solve(ctx, rp, c, v, b, api.CG_FP32_IR, rtol=rtol, inner_rtol=0.0)
     assert res["true_rel_residual"] <= rtol
     assert res["outer_iterations"] <= 3
+
+
+def test_cg_nan_rhs_reports_breakdown(ctx):
+    """A NaN in b makes <p, Ap> non-finite at the first iteration: the solver
+    stops with BREAKDOWN instead of iterating on NaNs."""
+    from paper_2204_02064_gb300 import api
+    rp, c, v = inputs.csr_spd_matrix(500, 9)
+    b = inputs.cg_rhs(500, 9)
+    b[17] = np.nan
+    with pytest.raises(api.PerksError) as ei:
+        _solve(ctx, rp, c, v, b, 0)
+    assert ei.value.name in ("BREAKDOWN", "NOT_CONVERGED")

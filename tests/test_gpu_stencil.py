@@ -369,3 +369,20 @@ def test_autotune_keeps_field_and_results(ctx, oracle, name, shape, dtype, varia
     st.get_field(out)
     torch.cuda.synchronize()
     assert rel_err(out.cpu().numpy(), oracle.stencil_run(f, offs, w, 9)) <= TOL[dtype]
+
+
+def test_barrier_benchmark_and_oversized_plan(ctx):
+    """The grid barrier costs microseconds per step at full occupancy; a
+    grid larger than the co-resident maximum is refused before any launch."""
+    from paper_2204_02064_gb300 import api
+    sms = ctx.info()["sm_count"]
+    us = ctx.barrier_benchmark(sms, 512, 500)
+    assert 0.05 < us < 50.0
+    with pytest.raises(api.PerksError) as ei:
+        ctx.barrier_benchmark(64 * sms, 1024, 10)
+    assert ei.value.name == "LAUNCH_TOO_LARGE"
+    st = api.Stencil(ctx, (64, 64, 64), inputs.shape_offsets("3d7pt"), inputs.workload_weights("3d7pt"))
+    st.set_plan(tiles=(16, 16, 16))  # 4096 blocks: more than one per SM can host
+    with pytest.raises(api.PerksError) as ei:
+        st.run(2, variant=0, stats=True)
+    assert ei.value.name in ("UNSUPPORTED", "LAUNCH_TOO_LARGE")
