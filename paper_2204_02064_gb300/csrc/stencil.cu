@@ -34,7 +34,7 @@ const ShapeInfo &shape_by_id(int id) {
     static const ShapeInfo table[kNumShapes] = {
         shape_info<S2d5>("2d5pt"),   shape_info<S3d7>("3d7pt"),  shape_info<S2d9>("2d9pt"),
         shape_info<S2d25>("2d25pt"), shape_info<S2ds9>("2ds9pt"), shape_info<S3d27>("3d27pt"),
-        shape_info<S3d13>("3d13pt")};
+        shape_info<S3d13>("3d13pt"), shape_info<S3d19>("poisson")};
     return table[id];
 }
 
@@ -46,7 +46,8 @@ int shape_uoff(int id, int i, int axis) {
     case 3: return S2d25::uoff(i, axis);
     case 4: return S2ds9::uoff(i, axis);
     case 5: return S3d27::uoff(i, axis);
-    default: return S3d13::uoff(i, axis);
+    case 6: return S3d13::uoff(i, axis);
+    default: return S3d19::uoff(i, axis);
     }
 }
 
@@ -90,6 +91,8 @@ std::vector<KernelEntry> &registry() {
         table.push_back(entry<float, S3d27, 1024, 0>(PERKS_F32, SH_3D27));
         table.push_back(entry<double, S3d13, 1024, 0>(PERKS_F64, SH_3D13));
         table.push_back(entry<float, S3d13, 1024, 0>(PERKS_F32, SH_3D13));
+        table.push_back(entry<double, S3d19, 1024, 0>(PERKS_F64, SH_3D19));
+        table.push_back(entry<float, S3d19, 1024, 0>(PERKS_F32, SH_3D19));
         // vectorised kernels: x extent a multiple of V (16-byte vectors)
         register_vec_f64_core(table);
         register_vec_f64_box2d(table);
@@ -100,6 +103,9 @@ std::vector<KernelEntry> &registry() {
         register_vec_bf16_core(table);
         register_vec_bf16_box2d(table);
         register_vec_bf16_box3d(table);
+        register_vec_f64_poisson(table);
+        register_vec_f32_poisson(table);
+        register_vec_bf16_poisson(table);
     }
     return table;
 }
@@ -194,7 +200,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     if (st->shape_id < 0)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "persistent kernel: offsets do not match a compiled shape "
-                    "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt)");
+                    "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt, poisson)");
     const ShapeInfo &sh = shape_by_id(st->shape_id);
     bool want_reg = true, allow_vec = true;
     int want_p = 0;

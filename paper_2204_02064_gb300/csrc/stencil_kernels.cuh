@@ -36,19 +36,49 @@ constexpr int kMaxKernelPoints = 27;
 // Compile-time stencil shape.  Offsets are listed in the user's canonical
 // order (centre, then -x,+x,-y,+y[,-z,+z] per distance for stars; row-major
 // x-fastest for boxes) and mapped to the internal orientation by `off`.
-template <int NDIM_, int R_, bool BOX_> struct Shape {
+// Stencil shape: NDIM-dimensional, radius R; KIND 0 = star (centre plus
+// +-1..R along each axis), 1 = full box, 2 = box without its corners (the
+// 3-D 19-point "poisson" stencil of Table 3: centre, 6 faces, 12 edges).
+// BOX = the shape reaches diagonal neighbours (corner halos are needed).
+template <int NDIM_, int R_, int KIND_> struct Shape {
     static constexpr int NDIM = NDIM_;
     static constexpr int R = R_;
-    static constexpr bool BOX = BOX_;
+    static constexpr int KIND = KIND_;
+    static constexpr bool BOX = KIND_ != 0;
     static constexpr int W = 2 * R + 1;
-    static constexpr int NPTS = BOX ? (NDIM == 3 ? W * W * W : W * W) : 1 + 2 * NDIM * R;
+    static constexpr int NBOX = NDIM == 3 ? W * W * W : W * W;
+    __host__ __device__ static constexpr bool is_corner(int b) {
+        const int ix = b % W, iy = (b / W) % W, iz = b / (W * W);
+        return (ix == 0 || ix == W - 1) && (iy == 0 || iy == W - 1) && (NDIM != 3 || iz == 0 || iz == W - 1);
+    }
+    __host__ __device__ static constexpr int count_points() {
+        if (KIND == 0) return 1 + 2 * NDIM * R;
+        if (KIND == 1) return NBOX;
+        int n = 0;
+        for (int b = 0; b < NBOX; ++b)
+            if (!is_corner(b)) ++n;
+        return n;
+    }
+    static constexpr int NPTS = count_points();
     static constexpr int RX = R;
     static constexpr int RY = NDIM == 3 ? R : 0;
     static constexpr int RZ = R;
+    // box index of point i (KIND 1, 2): row-major over (x, y, z), corners skipped for KIND 2
+    __host__ __device__ static constexpr int box_index(int i) {
+        if (KIND == 1) return i;
+        int n = 0;
+        for (int b = 0; b < NBOX; ++b) {
+            if (is_corner(b)) continue;
+            if (n == i) return b;
+            ++n;
+        }
+        return 0;
+    }
     // user-orientation offset of point i
     __host__ __device__ static constexpr int uoff(int i, int axis) {
         if (BOX) {
-            const int ix = i % W, iy = (i / W) % W, iz = i / (W * W);
+            const int b = box_index(i);
+            const int ix = b % W, iy = (b / W) % W, iz = b / (W * W);
             return axis == 0 ? ix - R : axis == 1 ? iy - R : (NDIM == 3 ? iz - R : 0);
         }
         if (i == 0) return 0;

@@ -74,12 +74,18 @@ SHAPES = {
     "3d7pt": ("star", 3, 1),
     "3d13pt": ("star", 3, 2),
     "3d27pt": ("box", 3, 1),
+    "poisson": ("box19", 3, 1),  # Table 3's 19-point stencil: centre, 6 faces, 12 edges
 }
 
 
 def shape_offsets(name: str) -> list[tuple[int, int, int]]:
     kind, ndim, r = SHAPES[name]
-    return star_offsets(ndim, r) if kind == "star" else box_offsets(ndim, r)
+    if kind == "star":
+        return star_offsets(ndim, r)
+    offs = box_offsets(ndim, r)
+    if kind == "box19":  # the box without its 8 corners
+        offs = [o for o in offs if not all(abs(d) == r for d in o)]
+    return offs
 
 
 def workload_weights(name: str, seed: int = 0) -> np.ndarray:

@@ -79,6 +79,7 @@ CASES = [
     ("2ds9pt", (97, 130), 12),
     ("3d27pt", (29, 33, 40), 6),
     ("3d13pt", (29, 33, 40), 6),
+    ("poisson", (29, 33, 40), 6),
 ]
 
 
@@ -248,6 +249,7 @@ LOWP_CASES = [
     ("2ds9pt", (97, 128), 9),
     ("3d27pt", (29, 33, 40), 5),
     ("3d13pt", (29, 33, 40), 5),
+    ("poisson", (29, 33, 40), 5),
 ]
 
 

@@ -230,3 +230,23 @@ def test_lowp_bf16_values_are_bf16_and_constant_preserved(oracle):
     # bf16 results track the fp64 oracle to a few bf16 ulps per step
     ref = oracle.stencil_run(g.astype(np.float64), inputs.shape_offsets("2d5pt"), [0.2] * 5, 7)
     assert np.max(np.abs(o2 - ref)) <= 7 * 2.0 ** -8
+
+
+def test_poisson19_sine_mode_eigenvalue(oracle):
+    """Table 3's 19-point stencil (centre, faces, edges) with weights that
+    depend only on the offset's class: a product of sines vanishing on the
+    Dirichlet-0 ghost layer is an eigenvector, with eigenvalue
+    w_c + 2 w_f sum_d cos k_d + 4 w_e sum_{d<e} cos k_d cos k_e
+    (the +-o pairs of each class combine into cosines)."""
+    L = (6, 7, 9)  # z, y, x extents
+    kx, ky, kz = (np.pi * 2 / (L[2] + 1), np.pi * 3 / (L[1] + 1), np.pi * 1 / (L[0] + 1))
+    ix, iy, iz = (np.arange(1, n + 1) for n in (L[2], L[1], L[0]))
+    u = np.sin(kz * iz)[:, None, None] * np.sin(ky * iy)[None, :, None] * np.sin(kx * ix)[None, None, :]
+    offs = inputs.shape_offsets("poisson")
+    wc, wf, we = 0.28, 0.07, 0.025
+    w = [wc if sum(map(abs, o)) == 0 else (wf if sum(map(abs, o)) == 1 else we) for o in offs]
+    cx, cy, cz = np.cos(kx), np.cos(ky), np.cos(kz)
+    lam = wc + 2 * wf * (cx + cy + cz) + 4 * we * (cx * cy + cx * cz + cy * cz)
+    steps = 7
+    out = oracle.stencil_run(u, offs, w, steps)
+    assert np.max(np.abs(out - lam ** steps * u)) <= 1e-13 * np.max(np.abs(u))
