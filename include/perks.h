@@ -110,7 +110,9 @@ enum { PERKS_PERSISTENT = 0, PERKS_PER_STEP = 1 };
 typedef struct {
     int32_t ndim;                       /* 2 or 3 */
     int64_t nx, ny, nz;                 /* interior extents; nz must be 1 when ndim == 2 */
-    int32_t radius;                     /* 1 or 2: ghost ring width, max |offset| */
+    int32_t radius;                     /* 1..4: ghost ring width, max |offset|; the persistent
+                                           kernels cover radius 1 and 2 (the compiled shapes), larger
+                                           radii run the per-step variant only */
     int32_t npts;                       /* number of (offset, weight) pairs, 1..PERKS_MAX_POINTS */
     int32_t offsets[3 * PERKS_MAX_POINTS]; /* (dx, dy, dz) per point; dz = 0 in 2-D */
     double weights[PERKS_MAX_POINTS];   /* w_o, applied in the storage dtype's accumulator */

@@ -509,8 +509,8 @@ extern "C" perks_status perks_stencil_create(perks_context *ctx, const perks_ste
         return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: bad extents");
     if (d->nx > INT32_MAX / 2 || d->ny > INT32_MAX / 2 || d->nz > INT32_MAX / 2)
         return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: extent too large");
-    if (d->radius < 1 || d->radius > 2)
-        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: radius must be 1 or 2");
+    if (d->radius < 1 || d->radius > 4)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: radius must be 1..4");
     if (d->npts < 1 || d->npts > PERKS_MAX_POINTS)
         return fail(ctx, PERKS_ERR_INVALID_ARG, "stencil_create: npts out of range");
     for (int i = 0; i < d->npts; ++i)

@@ -69,6 +69,8 @@ SHAPES = {
     # name: (kind, ndim, radius) -- the benchmark names of Table 3
     "2d5pt": ("star", 2, 1),
     "2ds9pt": ("star", 2, 2),
+    "2d13pt": ("star", 2, 3),
+    "2d17pt": ("star", 2, 4),
     "2d9pt": ("box", 2, 1),
     "2d25pt": ("box", 2, 2),
     "3d7pt": ("star", 3, 1),

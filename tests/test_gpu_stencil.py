@@ -388,3 +388,17 @@ def test_barrier_benchmark_and_oversized_plan(ctx):
     with pytest.raises(api.PerksError) as ei:
         st.run(2, variant=0, stats=True)
     assert ei.value.name in ("UNSUPPORTED", "LAUNCH_TOO_LARGE")
+
+
+@pytest.mark.parametrize("name,shape", [("2d13pt", (70, 90)), ("2d17pt", (53, 64))])
+def test_high_order_2d_stars_per_step(ctx, oracle, name, shape):
+    """Table 3's order-3 and order-4 2-D stars run the per-step variant
+    (generic kernel) against the oracle; the persistent variant reports
+    UNSUPPORTED (no compiled shape of radius > 2)."""
+    from paper_2204_02064_gb300 import api
+    f = inputs.stencil_field(shape, 39)
+    out, _ = _run_gpu(ctx, name, f, 7, variant=1)
+    assert rel_err(out, _oracle(oracle, name, f, 7)) <= 1e-12
+    with pytest.raises(api.PerksError) as ei:
+        _run_gpu(ctx, name, f, 7, variant=0)
+    assert ei.value.name == "UNSUPPORTED"
