@@ -445,7 +445,8 @@ def main():
     ap.add_argument("--profile", default=None,
                     help="run one small case for ncu and exit: headline, stencil3d-f64, "
                          "stencil3d-f32, stencil3d-bf16, stencil3d-f64-perstep, "
-                         "stencil3d-f32-perstep, cg-fp64, cg-fp32ir")
+                         "stencil3d-f32-perstep, stencil384-*, cg-fp64, cg-fp32ir, warmnet-tc, "
+                         "batch64, poisson")
     ap.add_argument("--leg", default=None, choices=["warmstart"],
                     help="run one extra workload and print its JSON (warmstart: the learned "
                          "warm start for the 512^2 x 256 Poisson problems)")
@@ -684,6 +685,42 @@ def profile_case(name):
             x = torch.zeros(n, dtype=torch.float64, device="cuda")
             r = op.solve(b, x, rtol=1e-10, mode=mode, max_iter=20, raise_on_error=False)
         print(json.dumps({"case": name, "n": n, "result": r}))
+    elif name == "warmnet-tc":
+        # the tensor-core inner layers: 32 images of 256^2, bf16 storage
+        n, m = 256, 32
+        k, f = inputs.poisson_problems_device(n, m, seed=inputs.SEED_POISSON, ell=16.0)
+        net = api.WarmNet(ctx, storage=api.BF16, seed=7)
+        u = torch.zeros_like(f)
+        net.predict(k, f, u)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("capture")
+        net.predict(k, f, u)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": name, "images": m, "n": n}))
+    elif name == "batch64":
+        doms = inputs.batch_domains()
+        b = api.Batch(ctx, doms, dtype="f32")
+        for j, d in enumerate(doms):
+            b.set_field(j, torch.from_numpy(inputs.stencil_field(d["shape"], d["seed"])).float().cuda())
+        b.autotune(5)
+        b.run(20, stats=True)
+        torch.cuda.nvtx.range_push("capture")
+        st = b.run(20, stats=True)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": name, "stats": st}))
+    elif name == "poisson":
+        k, f = inputs.poisson_problems_device(512, 256, seed=inputs.SEED_POISSON)
+        P = api.Poisson(ctx, k)
+        x = torch.zeros_like(f)
+        P.solve(f, x, rtol=1e-8, max_iter=50, stats=False)
+        x.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("capture")
+        P.solve(f, x, rtol=1e-8, max_iter=50, stats=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": name, "problems": 256, "n": 512, "iterations": 50}))
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
