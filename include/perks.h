@@ -401,6 +401,10 @@ perks_status perks_poisson_apply(perks_poisson *p, const double *v, double *y, p
  * then returns the first failing problem's status. */
 perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, double rtol,
                                  int32_t max_iter, perks_stream stream, perks_poisson_stats *stats);
+/* Block shape of the solve: 256 threads (two blocks per SM, default) or 512
+ * (one block per SM: half as many problems at a time, twice the loads in
+ * flight per problem).  Errors: INVALID_ARG. */
+perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
 
 
 /* ------------------------------------------------------------------------ */

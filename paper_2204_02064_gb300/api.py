@@ -133,6 +133,7 @@ def _declare(lib):
         "perks_poisson_destroy": ([P], i32),
         "perks_poisson_apply": ([P, P, P, P], i32),
         "perks_poisson_solve": ([P, P, P, f64, i32, P, ctypes.POINTER(PoissonStats)], i32),
+        "perks_poisson_set_block_threads": ([P, i32], i32),
         "perks_warmnet_create": ([P, P, i32, ctypes.c_uint64, ctypes.POINTER(P)], i32),
         "perks_warmnet_destroy": ([P], i32),
         "perks_warmnet_num_params": ([P], i32),
@@ -590,6 +591,10 @@ class Poisson:
         if not (vd and yd):
             raise ValueError("apply takes device tensors")
         self.ctx.check(self._lib.perks_poisson_apply(self.handle, vp, yp, _stream(stream)))
+
+    def set_block_threads(self, threads: int):
+        """256 (two blocks per SM, default) or 512 threads per problem's block."""
+        self.ctx.check(self._lib.perks_poisson_set_block_threads(self.handle, int(threads)))
 
     def solve(self, b, x, rtol: float = 1e-8, max_iter: int = 20000, stream=None, stats: bool = True):
         bp, bd, _ = _buffer(b)

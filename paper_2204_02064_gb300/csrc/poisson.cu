@@ -153,18 +153,18 @@ constexpr int kLin = 2;
 
 // r = b - A x over the whole problem; returns this thread's partial <r,r>
 // (and <b,b> through bb); optionally p = r.
-template <bool SET_P>
+template <bool SET_P, int ROWS>
 __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, const double *__restrict__ fyp,
                                                 const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *__restrict__ p, int nx, int ny,
                                                 double &bb) {
     double rr = 0.0;
-    for (int j0 = 0; j0 < ny; j0 += kRows)
+    for (int j0 = 0; j0 < ny; j0 += ROWS)
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            double rv[kRows], bv[kRows], xc[kRows];
-            apply_column<kRows>(fxp, fyp, x, nx, ny, i, j0, rv, xc);
+            double rv[ROWS], bv[ROWS], xc[ROWS];
+            apply_column<ROWS>(fxp, fyp, x, nx, ny, i, j0, rv, xc);
 #pragma unroll
-            for (int u = 0; u < kRows; ++u) {
+            for (int u = 0; u < ROWS; ++u) {
                 const int j = j0 + u;
                 if (j < ny) {
                     const long long c = (long long)j * nx + i;
@@ -173,7 +173,7 @@ __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, 
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kRows; ++u) {
+            for (int u = 0; u < ROWS; ++u) {
                 const int j = j0 + u;
                 if (j < ny) {
                     const long long c = (long long)j * nx + i;
@@ -187,7 +187,8 @@ __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, 
     return rr;
 }
 
-__global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const __grid_constant__ PoissonArgs a) {
+template <int NT, int MINB, int ROWS, int LIN>
+__global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid_constant__ PoissonArgs a) {
     __shared__ double red[33];
     __shared__ int s_prob;
     const int nx = a.nx, ny = a.ny;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
         double *__restrict__ q = a.q + pb * n;
         // r = b - A x, p = r
         double bb = 0.0;
-        double rr = residual_pass<true>(fxp, fyp, b, x, r, p, nx, ny, bb);
+        double rr = residual_pass<true, ROWS>(fxp, fyp, b, x, r, p, nx, ny, bb);
         bb = bsum(bb, red);
         rr = bsum(rr, red);
         const double tol2 = a.rtol * a.rtol * bb;
@@ -218,12 +219,12 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
             while (it < a.max_iter) {
                 // q = A p, <p, q>
                 double pq = 0.0;
-                for (int j0 = 0; j0 < ny; j0 += kRows)
+                for (int j0 = 0; j0 < ny; j0 += ROWS)
                     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                        double qv[kRows], pv[kRows];
-                        apply_column<kRows>(fxp, fyp, p, nx, ny, i, j0, qv, pv);
+                        double qv[ROWS], pv[ROWS];
+                        apply_column<ROWS>(fxp, fyp, p, nx, ny, i, j0, qv, pv);
 #pragma unroll
-                        for (int u = 0; u < kRows; ++u) {
+                        for (int u = 0; u < ROWS; ++u) {
                             const int j = j0 + u;
                             if (j < ny) {
                                 q[(long long)j * nx + i] = qv[u];
@@ -236,15 +237,15 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
                 const double alpha = rr / pq;
                 // x += alpha p, r -= alpha q, <r, r>
                 double rn = 0.0;
-                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * kLin) {
-                    double xv[kLin], rv[kLin], pv[kLin], qv[kLin];
+                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * LIN) {
+                    double xv[LIN], rv[LIN], pv[LIN], qv[LIN];
 #pragma unroll
-                    for (int u = 0; u < kLin; ++u) {
+                    for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
                         if (c < n) { xv[u] = x[c]; rv[u] = r[c]; pv[u] = p[c]; qv[u] = q[c]; }
                     }
 #pragma unroll
-                    for (int u = 0; u < kLin; ++u) {
+                    for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
                         if (c < n) {
                             x[c] = fma(alpha, pv[u], xv[u]);
@@ -257,15 +258,15 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
                 rn = bsum(rn, red);
                 const double beta = rn / rr;
                 // p = r + beta p
-                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * kLin) {
-                    double rv[kLin], pv[kLin];
+                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * LIN) {
+                    double rv[LIN], pv[LIN];
 #pragma unroll
-                    for (int u = 0; u < kLin; ++u) {
+                    for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
                         if (c < n) { rv[u] = r[c]; pv[u] = p[c]; }
                     }
 #pragma unroll
-                    for (int u = 0; u < kLin; ++u) {
+                    for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
                         if (c < n) p[c] = fma(beta, pv[u], rv[u]);
                     }
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kPoiThreads, 2) perks_poisson_cg_kernel(const 
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             double bdum = 0.0;
-            rr = bsum(residual_pass<true>(fxp, fyp, b, x, r, p, nx, ny, bdum), red);
+            rr = bsum(residual_pass<true, ROWS>(fxp, fyp, b, x, r, p, nx, ny, bdum), red);
             if (rr <= tol2) { status = PERKS_OK; break; }
             if (!converged || restart >= a.max_restarts) break;
         }
@@ -311,6 +312,7 @@ struct perks_poisson {
     double *fx = nullptr, *fy = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     int *queue = nullptr, *iters = nullptr, *status = nullptr;
     double *true_rel = nullptr;
+    int block_threads = kPoiThreads;  // 256 (two blocks per SM) or 512 (one, deeper loads)
 };
 
 namespace {
@@ -407,12 +409,13 @@ extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, d
     a.rtol = rtol;
     a.max_iter = max_iter;
     a.max_restarts = 8;
+    const void *kern = P->block_threads == 512 ? (const void *)perks_poisson_cg_kernel<512, 1, 4, 2>
+                                               : (const void *)perks_poisson_cg_kernel<kPoiThreads, 2, 4, 2>;
     int per_sm = 0;
-    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)perks_poisson_cg_kernel,
-                                                                  kPoiThreads, 0));
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P->block_threads, 0));
     const int grid = std::max(1, std::min(P->nprob, per_sm * ctx->sm_count));
-    perks_poisson_cg_kernel<<<grid, kPoiThreads, 0, s>>>(a);
-    PERKS_CUDA(ctx, cudaGetLastError());
+    void *kargs[] = {(void *)&a};
+    PERKS_CUDA(ctx, cudaLaunchKernel(kern, dim3(grid), dim3(P->block_threads), kargs, 0, s));
     PERKS_CUDA(ctx, cudaMemcpyAsync(x, P->x, vb, cudaMemcpyDeviceToDevice, s));
     if (!stats) return PERKS_OK;
     PERKS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -448,5 +451,13 @@ extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, d
     delete[] st;
     delete[] tr;
     if (worst != PERKS_OK) return fail(ctx, worst, "poisson_solve: a problem did not converge (status %d)", worst);
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_set_block_threads(perks_poisson *P, int32_t threads) {
+    if (!P) return PERKS_ERR_INVALID_ARG;
+    if (threads != 256 && threads != 512)
+        return fail(P->ctx, PERKS_ERR_INVALID_ARG, "poisson_set_block_threads: 256 or 512");
+    P->block_threads = threads;
     return PERKS_OK;
 }

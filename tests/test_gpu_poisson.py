@@ -64,3 +64,21 @@ def test_warm_start_with_exact_solution_needs_no_iteration(ctx, oracle):
     x = torch.from_numpy(u).cuda()
     res = P.solve(b, x, rtol=1e-8)
     assert res["max_iterations"] == 0
+
+
+def test_block_shapes_agree(ctx):
+    """256- and 512-thread blocks solve the same problems to the tolerance
+    with the same iteration counts (+-2: block sums in another order)."""
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 7, 40, 52
+    k = _k(nprob, ny, nx, 5)
+    f = 2.0 * inputs.uniform(6, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
+    res = []
+    for threads in (256, 512):
+        P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+        P.set_block_threads(threads)
+        x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+        r = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
+        assert r["max_true_rel_residual"] <= 1e-8
+        res.append(r["iterations"])
+    assert np.max(np.abs(res[0] - res[1])) <= 2
