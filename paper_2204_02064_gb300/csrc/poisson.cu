@@ -27,6 +27,7 @@ struct PoissonArgs {
     long long n;                 // cells per problem
     const double *fx;            // [prob][ny][nx+1] x-face coefficients
     const double *fy;            // [prob][ny+1][nx] y-face coefficients
+    const double *dg;            // [prob][n] diagonal: (fw + fe) + (fs + fn) of each cell
     const double *b;             // [prob][n]
     double *x, *r, *p, *q;       // [prob][n]
     double rtol;
@@ -72,15 +73,33 @@ __global__ void poisson_faces_kernel(const double *__restrict__ k, int nx, int n
     }
 }
 
+// Diagonal of every cell, (fw + fe) + (fs + fn), computed once: the matvec
+// then needs one multiply and four fused multiply-adds per cell (the FP64
+// pipe, not HBM, bounds this CG on GB300).
+__global__ void poisson_diag_kernel(const double *__restrict__ fx, const double *__restrict__ fy, int nx, int ny,
+                                    long long total_cells, double *dg) {
+    const long long n = (long long)nx * ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total_cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long pb = t / n, c = t % n;
+        const int j = (int)(c / nx), i = (int)(c % nx);
+        const double *fxp = fx + pb * (long long)(nx + 1) * ny;
+        const double *fyp = fy + pb * (long long)nx * (ny + 1);
+        const double fw = fxp[(long long)j * (nx + 1) + i], fe = fxp[(long long)j * (nx + 1) + i + 1];
+        const double fs = fyp[(long long)j * nx + i], fn = fyp[(long long)(j + 1) * nx + i];
+        dg[t] = (fw + fe) + (fs + fn);
+    }
+}
+
 // (A v)_c for cell c = (i, j) of one problem.
 __device__ __forceinline__ double apply_cell(const double *__restrict__ fxp, const double *__restrict__ fyp,
-                                             const double *__restrict__ v, int nx, int ny, int i, int j) {
+                                             const double *__restrict__ dgp, const double *__restrict__ v, int nx,
+                                             int ny, int i, int j) {
     const long long c = (long long)j * nx + i;
     const double fw = fxp[(long long)j * (nx + 1) + i], fe = fxp[(long long)j * (nx + 1) + i + 1];
     const double fs = fyp[(long long)j * nx + i], fn = fyp[(long long)(j + 1) * nx + i];
     const double vc = v[c];
-    double s = (fw + fe) + (fs + fn);
-    double acc = s * vc;
+    double acc = dgp[c] * vc;
     if (i > 0) acc = fma(-fw, v[c - 1], acc);
     if (i + 1 < nx) acc = fma(-fe, v[c + 1], acc);
     if (j > 0) acc = fma(-fs, v[c - nx], acc);
@@ -94,8 +113,8 @@ __device__ __forceinline__ double apply_cell(const double *__restrict__ fxp, con
 // skipped.
 template <int K>
 __device__ __forceinline__ void apply_column(const double *__restrict__ fxp, const double *__restrict__ fyp,
-                                             const double *__restrict__ v, int nx, int ny, int i, int j0,
-                                             double (&out)[K], double (&vc)[K]) {
+                                             const double *__restrict__ dgp, const double *__restrict__ v, int nx,
+                                             int ny, int i, int j0, double (&out)[K], double (&vc)[K]) {
     double col[K + 2];
     double fyv[K + 1];
 #pragma unroll
@@ -117,7 +136,7 @@ __device__ __forceinline__ void apply_column(const double *__restrict__ fxp, con
             const double fw = __ldg(fr), fe = __ldg(fr + 1);
             const double fs = fyv[u], fn = fyv[u + 1];
             const double vcen = col[u + 1];
-            double acc = ((fw + fe) + (fs + fn)) * vcen;
+            double acc = __ldg(dgp + c) * vcen;
             if (i > 0) acc = fma(-fw, v[c - 1], acc);
             if (i + 1 < nx) acc = fma(-fe, v[c + 1], acc);
             if (j > 0) acc = fma(-fs, col[u], acc);
@@ -155,6 +174,7 @@ constexpr int kLin = 2;
 // (and <b,b> through bb); optionally p = r.
 template <bool SET_P, int ROWS>
 __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, const double *__restrict__ fyp,
+                                                const double *__restrict__ dgp,
                                                 const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *__restrict__ p, int nx, int ny,
                                                 double &bb) {
@@ -162,7 +182,7 @@ __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, 
     for (int j0 = 0; j0 < ny; j0 += ROWS)
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double rv[ROWS], bv[ROWS], xc[ROWS];
-            apply_column<ROWS>(fxp, fyp, x, nx, ny, i, j0, rv, xc);
+            apply_column<ROWS>(fxp, fyp, dgp, x, nx, ny, i, j0, rv, xc);
 #pragma unroll
             for (int u = 0; u < ROWS; ++u) {
                 const int j = j0 + u;
@@ -201,6 +221,7 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
         if (pb >= a.nprob) break;
         const double *__restrict__ fxp = a.fx + (long long)pb * (nx + 1) * ny;
         const double *__restrict__ fyp = a.fy + (long long)pb * nx * (ny + 1);
+        const double *__restrict__ dgp = a.dg + (long long)pb * n;
         const double *__restrict__ b = a.b + pb * n;
         double *__restrict__ x = a.x + pb * n;
         double *__restrict__ r = a.r + pb * n;
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
         double *__restrict__ q = a.q + pb * n;
         // r = b - A x, p = r
         double bb = 0.0;
-        double rr = residual_pass<true, ROWS>(fxp, fyp, b, x, r, p, nx, ny, bb);
+        double rr = residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, bb);
         bb = bsum(bb, red);
         rr = bsum(rr, red);
         const double tol2 = a.rtol * a.rtol * bb;
@@ -222,7 +243,7 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
                 for (int j0 = 0; j0 < ny; j0 += ROWS)
                     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
                         double qv[ROWS], pv[ROWS];
-                        apply_column<ROWS>(fxp, fyp, p, nx, ny, i, j0, qv, pv);
+                        apply_column<ROWS>(fxp, fyp, dgp, p, nx, ny, i, j0, qv, pv);
 #pragma unroll
                         for (int u = 0; u < ROWS; ++u) {
                             const int j = j0 + u;
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             double bdum = 0.0;
-            rr = bsum(residual_pass<true, ROWS>(fxp, fyp, b, x, r, p, nx, ny, bdum), red);
+            rr = bsum(residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, bdum), red);
             if (rr <= tol2) { status = PERKS_OK; break; }
             if (!converged || restart >= a.max_restarts) break;
         }
@@ -299,7 +320,7 @@ __global__ void poisson_apply_kernel(const __grid_constant__ PoissonArgs a, cons
         const long long pb = t / a.n, c = t % a.n;
         const double *fxp = a.fx + pb * (a.nx + 1) * a.ny;
         const double *fyp = a.fy + pb * a.nx * (a.ny + 1);
-        y[t] = apply_cell(fxp, fyp, v + pb * a.n, a.nx, a.ny, (int)(c % a.nx), (int)(c / a.nx));
+        y[t] = apply_cell(fxp, fyp, a.dg + pb * a.n, v + pb * a.n, a.nx, a.ny, (int)(c % a.nx), (int)(c / a.nx));
     }
 }
 
@@ -309,7 +330,8 @@ struct perks_poisson {
     perks_context *ctx = nullptr;
     int nx = 0, ny = 0, nprob = 0;
     long long n = 0;
-    double *fx = nullptr, *fy = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    double *fx = nullptr, *fy = nullptr, *dg = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr,
+           *q = nullptr;
     int *queue = nullptr, *iters = nullptr, *status = nullptr;
     double *true_rel = nullptr;
     int block_threads = kPoiThreads;  // 256 (two blocks per SM) or 512 (one, deeper loads)
@@ -317,7 +339,7 @@ struct perks_poisson {
 
 namespace {
 void free_poisson(perks_poisson *P) {
-    void *ptrs[] = {P->fx, P->fy, P->b, P->x, P->r, P->p, P->q, P->queue, P->iters, P->status, P->true_rel};
+    void *ptrs[] = {P->fx, P->fy, P->dg, P->b, P->x, P->r, P->p, P->q, P->queue, P->iters, P->status, P->true_rel};
     for (void *v : ptrs) if (v) cudaFree(v);
 }
 
@@ -325,7 +347,7 @@ PoissonArgs poisson_args(perks_poisson *P) {
     PoissonArgs a;
     std::memset(&a, 0, sizeof(a));
     a.nx = P->nx; a.ny = P->ny; a.nprob = P->nprob; a.n = P->n;
-    a.fx = P->fx; a.fy = P->fy; a.b = P->b; a.x = P->x; a.r = P->r; a.p = P->p; a.q = P->q;
+    a.fx = P->fx; a.fy = P->fy; a.dg = P->dg; a.b = P->b; a.x = P->x; a.r = P->r; a.p = P->p; a.q = P->q;
     a.queue = P->queue; a.iters = P->iters; a.true_rel = P->true_rel; a.status = P->status;
     return a;
 }
@@ -348,7 +370,7 @@ extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int
     const size_t fyb = sizeof(double) * (size_t)nx * (ny + 1) * nprob;
     double *kd = nullptr;
     cudaError_t e = cudaSuccess;
-    void **bufs[] = {(void **)&P->b, (void **)&P->x, (void **)&P->r, (void **)&P->p, (void **)&P->q};
+    void **bufs[] = {(void **)&P->b, (void **)&P->x, (void **)&P->r, (void **)&P->p, (void **)&P->q, (void **)&P->dg};
     for (void **bp : bufs) if (e == cudaSuccess) e = cudaMalloc(bp, vb);
     if (e == cudaSuccess) e = cudaMalloc(&P->fx, fxb);
     if (e == cudaSuccess) e = cudaMalloc(&P->fy, fyb);
@@ -367,6 +389,7 @@ extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int
         return cuda_fail(ctx, e, "poisson_create");
     }
     poisson_faces_kernel<<<1024, 256>>>(on_device ? k : kd, nx, ny, P->n * nprob, P->fx, P->fy);
+    poisson_diag_kernel<<<1024, 256>>>(P->fx, P->fy, nx, ny, P->n * nprob, P->dg);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (kd) cudaFree(kd);
