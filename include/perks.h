@@ -401,9 +401,11 @@ perks_status perks_poisson_apply(perks_poisson *p, const double *v, double *y, p
  * then returns the first failing problem's status. */
 perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, double rtol,
                                  int32_t max_iter, perks_stream stream, perks_poisson_stats *stats);
-/* Block shape of the solve: 256 threads (two blocks per SM, default) or 512
- * (one block per SM: half as many problems at a time, twice the loads in
- * flight per problem).  Errors: INVALID_ARG. */
+/* Block shape of the solve: 512 threads (one block per SM, default) or 256
+ * (two per SM: twice as many problems at a time, half the loads in flight
+ * per problem).  A batch finishes with its slowest problem running alone,
+ * where the larger block is faster (256 problems of 512^2: 23.6 s vs
+ * 31.8 s to 1e-8).  Errors: INVALID_ARG. */
 perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
 
 

@@ -593,7 +593,7 @@ class Poisson:
         self.ctx.check(self._lib.perks_poisson_apply(self.handle, vp, yp, _stream(stream)))
 
     def set_block_threads(self, threads: int):
-        """256 (two blocks per SM, default) or 512 threads per problem's block."""
+        """512 (one block per SM, default) or 256 threads per problem's block."""
         self.ctx.check(self._lib.perks_poisson_set_block_threads(self.handle, int(threads)))
 
     def solve(self, b, x, rtol: float = 1e-8, max_iter: int = 20000, stream=None, stats: bool = True):
