@@ -317,10 +317,21 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
             s = s >= S ? s - S : s;
             const T *rp = ring + (s * a.plane + tp.sidx + dyr * a.PW);
             const VT c = *reinterpret_cast<const VT *>(rp);
-            static_for<0, V>([&](auto JI) {
-                constexpr int j = decltype(JI)::value;
-                seg[r][R + j] = to_acc(c.v[j]);
-            });
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+                // two cells per conversion
+                const __nv_bfloat162 *c2 = reinterpret_cast<const __nv_bfloat162 *>(&c);
+                static_for<0, V / 2>([&](auto JI) {
+                    constexpr int j = decltype(JI)::value;
+                    const float2 f2 = __bfloat1622float2(c2[j]);
+                    seg[r][R + 2 * j] = f2.x;
+                    seg[r][R + 2 * j + 1] = f2.y;
+                });
+            } else {
+                static_for<0, V>([&](auto JI) {
+                    constexpr int j = decltype(JI)::value;
+                    seg[r][R + j] = to_acc(c.v[j]);
+                });
+            }
             // x-neighbour cells: from the adjacent lanes' vectors of the same
             // row by warp shuffles; lanes at a row or warp edge read the ring
             if constexpr (left) {
@@ -341,6 +352,7 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
             }
         });
         VT out;
+        A accs[V];
         static_for<0, V>([&](auto JI) {
             constexpr int j = decltype(JI)::value;
             A acc = A(0);
@@ -350,8 +362,21 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
                 constexpr int col = R + j + SH::dx(i);
                 acc = fma(ScalarOps<T>::w(a, i), seg[r][col], acc);
             });
-            out.v[j] = from_acc<T>(acc);
+            accs[j] = acc;
         });
+        if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+            // round to nearest even, two cells per conversion
+            __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&out);
+            static_for<0, V / 2>([&](auto JI) {
+                constexpr int j = decltype(JI)::value;
+                o2[j] = __floats2bfloat162_rn(accs[2 * j], accs[2 * j + 1]);
+            });
+        } else {
+            static_for<0, V>([&](auto JI) {
+                constexpr int j = decltype(JI)::value;
+                out.v[j] = from_acc<T>(accs[j]);
+            });
+        }
         bool to_field;
         if (STORE == PC_REG) {
             if constexpr (ZR > 0) regc[z < ZR ? z : 0] = out;
