@@ -34,7 +34,8 @@ const ShapeInfo &shape_by_id(int id) {
     static const ShapeInfo table[kNumShapes] = {
         shape_info<S2d5>("2d5pt"),   shape_info<S3d7>("3d7pt"),  shape_info<S2d9>("2d9pt"),
         shape_info<S2d25>("2d25pt"), shape_info<S2ds9>("2ds9pt"), shape_info<S3d27>("3d27pt"),
-        shape_info<S3d13>("3d13pt"), shape_info<S3d19>("poisson")};
+        shape_info<S3d13>("3d13pt"), shape_info<S3d19>("poisson"), shape_info<S2d13>("2d13pt"),
+        shape_info<S2d17>("2d17pt")};
     return table[id];
 }
 
@@ -47,7 +48,9 @@ int shape_uoff(int id, int i, int axis) {
     case 4: return S2ds9::uoff(i, axis);
     case 5: return S3d27::uoff(i, axis);
     case 6: return S3d13::uoff(i, axis);
-    default: return S3d19::uoff(i, axis);
+    case 7: return S3d19::uoff(i, axis);
+    case 8: return S2d13::uoff(i, axis);
+    default: return S2d17::uoff(i, axis);
     }
 }
 
@@ -106,6 +109,7 @@ std::vector<KernelEntry> &registry() {
         register_vec_f64_poisson(table);
         register_vec_f32_poisson(table);
         register_vec_bf16_poisson(table);
+        register_vec_star2d_hi(table);
     }
     return table;
 }
@@ -200,7 +204,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     if (st->shape_id < 0)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "persistent kernel: offsets do not match a compiled shape "
-                    "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 3d7pt, 3d13pt, 3d27pt, poisson)");
+                    "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 2d13pt, 2d17pt, 3d7pt, 3d13pt, 3d27pt, poisson)");
     const ShapeInfo &sh = shape_by_id(st->shape_id);
     bool want_reg = true, allow_vec = true;
     int want_p = 0;
@@ -220,6 +224,8 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
         kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, 0);
     if (!kp && body_per_step && !per_step)  // no vectorised cache-free body for this extent
         kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, false, st->X, allow_vec, want_p);
+    if (!kp && !per_step)  // shapes compiled with the cache-free body only (radius 3, 4)
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, true, st->X, allow_vec, 0);
     per_step = per_step || (kp && kp->per_step);
     if (!kp)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
@@ -240,7 +246,9 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     const int S = k.v > 1 ? 2 * RZ + k.p + k.d : 2 * RZ + 1 + k.d;  // ring slots (vector kernel: P planes per barrier)
     const int es = st->es;
     const int V = k.v;
-    const int HX = V > 1 ? std::max(V, 2) : RX;  // ring pad columns on each side
+    int HX = RX;  // ring pad columns on each side (vector kernel: a multiple of V, >= 2 and >= the radius)
+    if (V > 1)
+        for (HX = std::max(V, 2); HX < RX; HX += V) {}
     int per_sm = 0;
     PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, k.nt,
                                                                   k.smem_budget));

@@ -16,9 +16,11 @@ using S2ds9 = Shape<2, 2, false>;
 using S3d27 = Shape<3, 1, true>;
 using S3d13 = Shape<3, 2, false>;
 using S3d19 = Shape<3, 1, 2>;  // "poisson": box without corners
+using S2d13 = Shape<2, 3, 0>;  // high-order 2-D stars (cache-free body only)
+using S2d17 = Shape<2, 4, 0>;
 
 // shape ids (the order of the table in stencil.cu)
-enum ShapeId : int { SH_2D5 = 0, SH_3D7, SH_2D9, SH_2D25, SH_2DS9, SH_3D27, SH_3D13, SH_3D19, SH_COUNT };
+enum ShapeId : int { SH_2D5 = 0, SH_3D7, SH_2D9, SH_2D25, SH_2DS9, SH_3D27, SH_3D13, SH_3D19, SH_2D13, SH_2D17, SH_COUNT };
 
 using PersistentFn = void (*)(PersistentArgs);
 
@@ -46,5 +48,6 @@ void register_vec_bf16_box3d(std::vector<KernelEntry> &out);
 void register_vec_f64_poisson(std::vector<KernelEntry> &out);
 void register_vec_f32_poisson(std::vector<KernelEntry> &out);
 void register_vec_bf16_poisson(std::vector<KernelEntry> &out);
+void register_vec_star2d_hi(std::vector<KernelEntry> &out);
 
 }  // namespace perks

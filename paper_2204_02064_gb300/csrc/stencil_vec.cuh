@@ -114,7 +114,7 @@ enum DutyKind : int { DUTY_NONE = 0, DUTY_BND_VEC, DUTY_BND_PAIR, DUTY_FIELD_VEC
 struct VecPlan {
     int tile, x0, y0, z0, tx, ty, tz;
     bool own;
-    bool shl, shr;      // left / right x-neighbour cells come from lane-1 / lane+1 (same row)
+    int rowpos, nvx;    // position of the thread's vector in its row, vectors per row
     unsigned own_mask;  // lanes of this warp that own cells
     int lx0, ly;
     long long gxy;      // field offset of the thread's first cell at z = 0
@@ -129,13 +129,21 @@ struct VecPlan {
     long long wface_off, eface_off;  // own face entries (z = 0)
 };
 
-// Element layout of a ring slot row: HX pad cells, tx cells, HX pad cells.
-template <int V> __host__ __device__ constexpr int vec_hx() { return V >= 2 ? V : 2; }
+// Element layout of a ring slot row: HX pad cells, tx cells, HX pad cells
+// (HX a multiple of V, at least 2 and at least the radius).
+template <int V, int R = 1> __host__ __device__ constexpr int vec_hx() {
+    int hx = V >= 2 ? V : 2;
+    while (hx < R) hx += V;
+    return hx;
+}
+// Cells of one x-halo item (each side of a row): 2 up to radius 2, 4 beyond.
+template <int R> __host__ __device__ constexpr int vec_xw() { return R <= 2 ? 2 : 4; }
 
 template <class SH, int V, bool PER_STEP>
 __device__ __forceinline__ VecPlan make_vec_plan(const PersistentArgs &a, int tile) {
     constexpr int RY = SH::RY;
-    constexpr int HX = vec_hx<V>();
+    constexpr int HX = vec_hx<V, SH::R>();
+    constexpr int XW = vec_xw<SH::R>();
     VecPlan p;
     p.tile = tile;
     const int ti = p.tile % a.ntx, tj = (p.tile / a.ntx) % a.nty, tk = p.tile / (a.ntx * a.nty);
@@ -152,8 +160,8 @@ __device__ __forceinline__ VecPlan make_vec_plan(const PersistentArgs &a, int ti
     const int c = threadIdx.x;
     p.own = c < nvx * p.ty;
     p.own_mask = __ballot_sync(0xffffffffu, p.own);
-    p.shl = p.own && (c % nvx) > 0 && (c & 31) > 0;
-    p.shr = p.own && (c % nvx) + 1 < nvx && (c & 31) < 31;
+    p.rowpos = p.own ? c % nvx : 0;
+    p.nvx = nvx;
     p.lx0 = p.own ? (c % nvx) * V : 0;
     p.ly = p.own ? c / nvx : 0;
     p.gxy = (long long)(p.x0 + p.lx0) + (long long)(p.y0 + p.ly) * a.X;
@@ -183,13 +191,13 @@ __device__ __forceinline__ VecPlan make_vec_plan(const PersistentArgs &a, int ti
         const int k = c - n_yrow;
         const int r = k / 2;
         lyr = r < RY ? r - RY : p.ty + (r - RY);
-        lxr = (k % 2 == 0) ? -2 : p.tx;
+        lxr = (k % 2 == 0) ? -XW : p.tx;
         kind = DUTY_FIELD_PAIR;
     } else if (c < n_yrow + n_corner + n_xpair) {
         const int k = c - n_yrow - n_corner;
         const int side = k / p.ty;
         lyr = k % p.ty;
-        lxr = side == 0 ? -2 : p.tx;
+        lxr = side == 0 ? -XW : p.tx;
         kind = DUTY_XPAIR;
         if (!PER_STEP) {
             const int nb = side == 0 ? p.tile - 1 : p.tile + 1;
@@ -199,7 +207,7 @@ __device__ __forceinline__ VecPlan make_vec_plan(const PersistentArgs &a, int ti
     }
     if (kind != DUTY_NONE) {
         const int gx = p.x0 + lxr, gy = p.y0 + lyr;
-        const int width = kind == DUTY_FIELD_VEC ? V : 2;
+        const int width = kind == DUTY_FIELD_VEC ? V : XW;
         p.dsidx = (lyr + RY) * a.PW + HX + lxr;
         if (gy < 0 || gy >= a.Y || gx < 0 || gx + width > a.X) {
             p.duty = kind == DUTY_FIELD_VEC ? DUTY_BND_VEC : DUTY_BND_PAIR;
@@ -279,17 +287,23 @@ __device__ __forceinline__ void vfill_fast(const PersistentArgs &a, const VecPla
         }
     }
     const bool inside = FILL != PC_HALO;
+    constexpr int XW = vec_xw<SH::R>();
     if (tp.duty != DUTY_NONE && (inside || SH::BOX)) {
         T *d = sl + tp.dsidx;
         if (!in_z || tp.duty == DUTY_BND_VEC || tp.duty == DUTY_BND_PAIR) {
             if (tp.duty == DUTY_FIELD_VEC || tp.duty == DUTY_BND_VEC) set_vec<T, V>(d, bnd);
-            else { PT x; x.v[0] = bnd; x.v[1] = bnd; *reinterpret_cast<PT *>(d) = x; }
+            else
+                static_for<0, XW>([&](auto JI) { d[decltype(JI)::value] = bnd; });
         } else if (tp.duty == DUTY_FIELD_VEC) {
             copy_vec<T, V>(d, sp.fill_duty);
         } else if (tp.duty == DUTY_XPAIR && inside && !PER_STEP && (FILL != PC_GLOBAL || !a.faces_cached_only)) {
+            static_assert(XW == 2 || PER_STEP, "x-edge face buffers hold pairs: radius <= 2 for cached kernels");
             cp_async<sizeof(T) * 2>(d, sp.face_src);
-        } else {
-            cp_async<sizeof(T) * 2>(d, sp.fill_duty);
+        } else if constexpr (sizeof(T) * XW <= 16) {
+            cp_async<sizeof(T) * XW>(d, sp.fill_duty);
+        } else {  // fp64, 4 cells: two 16-byte copies
+            cp_async<16>(d, sp.fill_duty);
+            cp_async<16>(d + 16 / sizeof(T), sp.fill_duty + 16 / sizeof(T));
         }
     }
 }
@@ -334,19 +348,25 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
             }
             // x-neighbour cells: from the adjacent lanes' vectors of the same
             // row by warp shuffles; lanes at a row or warp edge read the ring
+            const int lane = threadIdx.x & 31;
             if constexpr (left) {
                 static_for<0, R>([&](auto JI) {
-                    constexpr int j = decltype(JI)::value;
-                    const A v = __shfl_up_sync(tp.own_mask, seg[r][V + j], 1);  // lane-1's cell V-R+j
-                    if (tp.shl) seg[r][j] = v;
+                    constexpr int j = decltype(JI)::value;      // cell at offset j - R
+                    constexpr int dist = R - j;                 // cells to the left
+                    constexpr int back = (dist + V - 1) / V;    // lanes back
+                    constexpr int el = V * back - dist;         // that lane's element
+                    const A v = __shfl_up_sync(tp.own_mask, seg[r][R + el], back);
+                    if (tp.rowpos >= back && lane >= back) seg[r][j] = v;
                     else seg[r][j] = to_acc(rp[j - R]);
                 });
             }
             if constexpr (right) {
                 static_for<0, R>([&](auto JI) {
-                    constexpr int j = decltype(JI)::value;
-                    const A v = __shfl_down_sync(tp.own_mask, seg[r][R + j], 1);  // lane+1's cell j
-                    if (tp.shr) seg[r][R + V + j] = v;
+                    constexpr int j = decltype(JI)::value;      // cell at offset V + j
+                    constexpr int fwd = j / V + 1;              // lanes forward
+                    constexpr int el = j - V * (fwd - 1);       // that lane's element
+                    const A v = __shfl_down_sync(tp.own_mask, seg[r][R + el], fwd);
+                    if (tp.rowpos + fwd < tp.nvx && lane + fwd < 32) seg[r][R + V + j] = v;
                     else seg[r][R + V + j] = to_acc(rp[V + j]);
                 });
             }

@@ -80,6 +80,9 @@ CASES = [
     ("3d27pt", (29, 33, 40), 6),
     ("3d13pt", (29, 33, 40), 6),
     ("poisson", (29, 33, 40), 6),
+    ("2d13pt", (70, 96), 9),           # radius 3 (Table 3's order-3 star)
+    ("2d17pt", (53, 64), 7),           # radius 4
+    ("2d17pt", (5, 8), 3),             # fewer rows than the radius
 ]
 
 
@@ -250,6 +253,8 @@ LOWP_CASES = [
     ("3d27pt", (29, 33, 40), 5),
     ("3d13pt", (29, 33, 40), 5),
     ("poisson", (29, 33, 40), 5),
+    ("2d13pt", (97, 128), 9),
+    ("2d17pt", (61, 136), 7),
 ]
 
 
@@ -390,15 +395,32 @@ def test_barrier_benchmark_and_oversized_plan(ctx):
     assert ei.value.name in ("UNSUPPORTED", "LAUNCH_TOO_LARGE")
 
 
-@pytest.mark.parametrize("name,shape", [("2d13pt", (70, 90)), ("2d17pt", (53, 64))])
-def test_high_order_2d_stars_per_step(ctx, oracle, name, shape):
-    """Table 3's order-3 and order-4 2-D stars run the per-step variant
-    (generic kernel) against the oracle; the persistent variant reports
-    UNSUPPORTED (no compiled shape of radius > 2)."""
+@pytest.mark.parametrize("plan", [
+    dict(tiles=(16, 1, 4), smem_cache_planes=0, reg_cache=0),   # 4-cell tiles: every x-neighbour from the halo
+    dict(tiles=(8, 1, 3), smem_cache_planes=0, reg_cache=0),    # 8-cell tiles: two lanes back / forward
+    dict(tiles=(3, 1, 7), smem_cache_planes=0, reg_cache=0),    # ragged tiles
+])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["2d13pt", "2d17pt"])
+def test_high_order_2d_star_tilings(ctx, oracle, name, dtype, plan):
+    """Radius 3 and 4 stars (Table 3) on narrow and ragged x tiles: the
+    x-neighbours come from lanes up to two vectors away or from the 4-cell
+    x-halo, and every tiling agrees with the oracle."""
+    f = inputs.stencil_field((45, 64), 39)
+    out, stats = _run_gpu(ctx, name, f, 8, dtype=dtype, plan=plan)
+    assert stats["tiles_x"] == plan["tiles"][0]
+    assert rel_err(out, _oracle(oracle, name, f, 8)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("name,shape", [("2d13pt", (70, 90)), ("2d17pt", (53, 66))])
+def test_high_order_2d_stars_unaligned_extent(ctx, oracle, name, shape):
+    """An x extent that is not a multiple of the vector width: the per-step
+    variant runs the generic kernel against the oracle; the persistent one,
+    compiled for the vectorised body only, reports UNSUPPORTED."""
     from paper_2204_02064_gb300 import api
     f = inputs.stencil_field(shape, 39)
-    out, _ = _run_gpu(ctx, name, f, 7, variant=1)
-    assert rel_err(out, _oracle(oracle, name, f, 7)) <= 1e-12
+    out, _ = _run_gpu(ctx, name, f, 7, dtype="f32", variant=1)
+    assert rel_err(out, _oracle(oracle, name, f, 7)) <= TOL["f32"]
     with pytest.raises(api.PerksError) as ei:
-        _run_gpu(ctx, name, f, 7, variant=0)
+        _run_gpu(ctx, name, f, 7, dtype="f32", variant=0)
     assert ei.value.name == "UNSUPPORTED"
