@@ -111,8 +111,10 @@ typedef struct {
     int32_t ndim;                       /* 2 or 3 */
     int64_t nx, ny, nz;                 /* interior extents; nz must be 1 when ndim == 2 */
     int32_t radius;                     /* 1..4: ghost ring width, max |offset|; the persistent
-                                           kernels cover radius 1 and 2 (the compiled shapes), larger
-                                           radii run the per-step variant only */
+                                           kernels cover the compiled shapes (radius 1 and 2, and
+                                           the 2-D stars of radius 3 and 4 with nx a multiple of
+                                           16 bytes, those without on-chip caches); other shapes
+                                           run the per-step variant only */
     int32_t npts;                       /* number of (offset, weight) pairs, 1..PERKS_MAX_POINTS */
     int32_t offsets[3 * PERKS_MAX_POINTS]; /* (dx, dy, dz) per point; dz = 0 in 2-D */
     double weights[PERKS_MAX_POINTS];   /* w_o, applied in the storage dtype's accumulator */
@@ -395,6 +397,13 @@ perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int32_t ny, in
 perks_status perks_poisson_destroy(perks_poisson *p);
 /* y = A v for every problem; v, y: device arrays of nprob*nx*ny doubles. */
 perks_status perks_poisson_apply(perks_poisson *p, const double *v, double *y, perks_stream stream);
+/* Scales each problem's guess x (device, nprob*nx*ny doubles, in place) by
+ * alpha = <x, b> / <x, A x>, the multiple of x closest to the solution of
+ * A u = b in the A-norm (a one-dimensional Galerkin projection): for a
+ * learned warm start, an error in its overall amplitude costs no CG
+ * iterations.  A problem whose <x, A x> is not positive and finite (x = 0)
+ * keeps its x.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+perks_status perks_poisson_scale_guess(perks_poisson *p, const double *b, double *x, perks_stream stream);
 /* Solves every problem to ||r|| <= rtol ||b|| from x (device arrays of
  * nprob*nx*ny doubles; x holds x0 and receives the solutions).  With stats
  * the stream is synchronized and the per-problem outcome reported; the call

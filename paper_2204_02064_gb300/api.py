@@ -134,6 +134,7 @@ def _declare(lib):
         "perks_poisson_apply": ([P, P, P, P], i32),
         "perks_poisson_solve": ([P, P, P, f64, i32, P, ctypes.POINTER(PoissonStats)], i32),
         "perks_poisson_set_block_threads": ([P, i32], i32),
+        "perks_poisson_scale_guess": ([P, P, P, P], i32),
         "perks_warmnet_create": ([P, P, i32, ctypes.c_uint64, ctypes.POINTER(P)], i32),
         "perks_warmnet_destroy": ([P], i32),
         "perks_warmnet_num_params": ([P], i32),
@@ -591,6 +592,15 @@ class Poisson:
         if not (vd and yd):
             raise ValueError("apply takes device tensors")
         self.ctx.check(self._lib.perks_poisson_apply(self.handle, vp, yp, _stream(stream)))
+
+    def scale_guess(self, b, x, stream=None):
+        """x <- (<x,b> / <x,Ax>) x per problem, in place: the multiple of the
+        guess closest to the solution in the A-norm."""
+        bp, bd, _ = _buffer(b)
+        xp, xd, _ = _buffer(x)
+        if not (bd and xd):
+            raise ValueError("scale_guess takes device tensors")
+        self.ctx.check(self._lib.perks_poisson_scale_guess(self.handle, bp, xp, _stream(stream)))
 
     def set_block_threads(self, threads: int):
         """512 (one block per SM, default) or 256 threads per problem's block."""

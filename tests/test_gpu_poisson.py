@@ -82,3 +82,34 @@ def test_block_shapes_agree(ctx):
         assert r["max_true_rel_residual"] <= 1e-8
         res.append(r["iterations"])
     assert np.max(np.abs(res[0] - res[1])) <= 2
+
+
+def test_scale_guess_matches_oracle(ctx, oracle):
+    """x <- (<x,b>/<x,Ax>) x per problem, with A the oracle's CSR form of the
+    operator; a zero guess stays zero and an exact solution is left as is."""
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 4, 29, 41
+    k = _k(nprob, ny, nx, 7)
+    f = 2.0 * inputs.uniform(8, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
+    x = inputs.uniform(9, nprob * ny * nx).reshape(nprob, ny, nx) - 0.3
+    x[3] = 0.0
+    rp, c, val = oracle.poisson_csr(k[2])
+    x[2] = oracle.cg(rp, c, val, f[2].ravel(), rtol=1e-13, max_iter=20000)["x"].reshape(ny, nx)
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    xd = torch.from_numpy(x.copy()).cuda()
+    P.scale_guess(torch.from_numpy(f).cuda(), xd)
+    xs = xd.cpu().numpy()
+    for i in range(3):
+        rp, c, val = oracle.poisson_csr(k[i])
+        ax = oracle.spmv(rp, c, val, x[i].ravel())
+        alpha = oracle.dot(x[i].ravel(), f[i].ravel()) / oracle.dot(x[i].ravel(), ax)
+        want = alpha * x[i]
+        assert np.max(np.abs(xs[i] - want)) <= 1e-12 * np.max(np.abs(want))
+        if i == 2:
+            assert abs(alpha - 1.0) <= 1e-10
+        else:  # the A-norm error against the solution does not grow
+            u = oracle.cg(rp, c, val, f[i].ravel(), rtol=1e-12, max_iter=20000)["x"]
+            def anorm(e):
+                return oracle.dot(e, oracle.spmv(rp, c, val, e))
+            assert anorm(u - xs[i].ravel()) <= anorm(u - x[i].ravel())
+    assert not xs[3].any()
