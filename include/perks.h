@@ -416,6 +416,17 @@ perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, d
  * where the larger block is faster (256 problems of 512^2: 23.6 s vs
  * 31.8 s to 1e-8).  Errors: INVALID_ARG. */
 perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
+/* Blocks per problem (1, 2, 4 or 8; default 1).  With C > 1 each problem's
+ * rows are split over a group of C blocks that meet at a bounded barrier of
+ * their own after every p update and in every dot product (the group's block
+ * sums are added in rank order, so all its blocks take the same decisions);
+ * the launch is cooperative.  A batch ends with its hardest problem running
+ * alone; a group runs it up to C times faster, at the price of fewer problems
+ * in flight.  Iteration counts may differ from C = 1 by rounding (another
+ * summation order).  A barrier wait past the context's timeout ends the solve
+ * with BARRIER_TIMEOUT (reported when stats are requested).  Errors:
+ * INVALID_ARG. */
+perks_status perks_poisson_set_group(perks_poisson *p, int32_t blocks);
 
 
 /* ------------------------------------------------------------------------ */

@@ -135,6 +135,7 @@ def _declare(lib):
         "perks_poisson_solve": ([P, P, P, f64, i32, P, ctypes.POINTER(PoissonStats)], i32),
         "perks_poisson_set_block_threads": ([P, i32], i32),
         "perks_poisson_scale_guess": ([P, P, P, P], i32),
+        "perks_poisson_set_group": ([P, i32], i32),
         "perks_warmnet_create": ([P, P, i32, ctypes.c_uint64, ctypes.POINTER(P)], i32),
         "perks_warmnet_destroy": ([P], i32),
         "perks_warmnet_num_params": ([P], i32),
@@ -605,6 +606,10 @@ class Poisson:
     def set_block_threads(self, threads: int):
         """512 (one block per SM, default) or 256 threads per problem's block."""
         self.ctx.check(self._lib.perks_poisson_set_block_threads(self.handle, int(threads)))
+
+    def set_group(self, blocks: int):
+        """Blocks per problem: 1 (default), 2, 4 or 8 (rows split over the group)."""
+        self.ctx.check(self._lib.perks_poisson_set_group(self.handle, int(blocks)))
 
     def solve(self, b, x, rtol: float = 1e-8, max_iter: int = 20000, stream=None, stats: bool = True):
         bp, bd, _ = _buffer(b)

@@ -4,11 +4,16 @@
 // solved by CG (the Sec. 2.2.2 recurrence) as ONE persistent launch.
 //
 // Problems are independent, so the batch needs no grid barrier: each block
-// owns one problem at a time (blocks pull problems from an atomic counter),
-// keeps its scalars and partial sums on chip and runs that problem's whole
-// CG loop -- SpMV (matrix-free, from precomputed face coefficients), dot
-// products and axpys -- with block-level reductions only.  The true residual
-// is recomputed in fp64 on exit and CG restarts while it is above tolerance.
+// (or group of C blocks) owns one problem at a time, pulling problems from an
+// atomic counter, keeps its scalars and partial sums on chip and runs that
+// problem's whole CG loop -- SpMV (matrix-free, from precomputed face
+// coefficients), dot products and axpys.  With C = 1 the reductions are
+// block-level only.  With C > 1 the problem's rows are split over the group's
+// blocks, which meet at a bounded barrier of their own after each p update
+// and in each dot product (block sums added in rank order, so every block of
+// the group takes the same decisions): a batch ends with its hardest problem
+// running alone, and a group runs it C times faster.  The true residual is
+// recomputed in fp64 on exit and CG restarts while it is above tolerance.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,6 +26,7 @@ using namespace perks;
 namespace {
 
 constexpr int kPoiThreads = 256;
+constexpr int kPoiMaxGroup = 8;  // blocks per problem, at most
 
 struct PoissonArgs {
     int nx, ny, nprob;
@@ -37,6 +43,12 @@ struct PoissonArgs {
     int *iters;                  // [prob] recurrence iterations
     double *true_rel;            // [prob] ||b - A x|| / ||b||
     int *status;                 // [prob]
+    int group;                   // blocks per problem (C)
+    unsigned long long *gbar;    // [groups] barrier counter of each block group
+    int *gprob;                  // [groups] problem taken by each group
+    double *gpart;               // [groups][2][C] block sums, double-buffered
+    DevError *err;
+    long long timeout_ns;
 };
 
 __global__ void poisson_faces_kernel(const double *__restrict__ k, int nx, int ny, long long total_cells,
@@ -177,9 +189,9 @@ __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, 
                                                 const double *__restrict__ dgp,
                                                 const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *__restrict__ p, int nx, int ny,
-                                                double &bb) {
+                                                int jb, int je, double &bb) {
     double rr = 0.0;
-    for (int j0 = 0; j0 < ny; j0 += ROWS)
+    for (int j0 = jb; j0 < je; j0 += ROWS)
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double rv[ROWS], bv[ROWS], xc[ROWS];
             apply_column<ROWS>(fxp, fyp, dgp, x, nx, ny, i, j0, rv, xc);
@@ -207,14 +219,51 @@ __device__ __forceinline__ double residual_pass(const double *__restrict__ fxp, 
     return rr;
 }
 
-template <int NT, int MINB, int ROWS, int LIN>
+// Rows [jb, je) of a problem owned by block `rank` of a group of C: row
+// blocks of ROWS rows split evenly.
+template <int ROWS>
+__device__ __forceinline__ void group_rows(int ny, int C, int rank, int &jb, int &je) {
+    const int nrb = (ny + ROWS - 1) / ROWS;
+    jb = min(ny, (int)((long long)nrb * rank / C) * ROWS);
+    je = min(ny, (int)((long long)nrb * (rank + 1) / C) * ROWS);
+}
+
+template <int NT, int MINB, int ROWS, int LIN, bool GROUP>
 __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid_constant__ PoissonArgs a) {
     __shared__ double red[33];
     __shared__ int s_prob;
     const int nx = a.nx, ny = a.ny;
     const long long n = a.n;
+    const int C = GROUP ? a.group : 1;
+    const int g = blockIdx.x / C, rank = blockIdx.x % C;
+    int jb = 0, je = ny;
+    if (GROUP) group_rows<ROWS>(ny, C, rank, jb, je);
+    const long long cb = (long long)jb * nx, ce = (long long)je * nx;
+    unsigned long long epoch = 0;
+    int nred = 0;
+    // the group's sum of a per-thread value: block sums, then the group's
+    // block sums in rank order (the same value in every block); false if the
+    // group barrier gave up
+    auto gsum = [&](double v, double &out) -> bool {
+        v = bsum(v, red);
+        if (!GROUP) { out = v; return true; }
+        double *slot = a.gpart + ((long long)g * 2 + (nred & 1)) * C;
+        ++nred;
+        if (threadIdx.x == 0) slot[rank] = v;
+        if (!grid_barrier(a.gbar + g, C, epoch, a.err, a.timeout_ns)) return false;
+        double t = 0.0;
+        for (int i = 0; i < C; ++i) t += __ldcg(slot + i);
+        out = t;
+        return true;
+    };
     for (;;) {
-        if (threadIdx.x == 0) s_prob = atomicAdd(a.queue, 1);
+        if (GROUP) {
+            if (rank == 0 && threadIdx.x == 0) a.gprob[g] = atomicAdd(a.queue, 1);
+            if (!grid_barrier(a.gbar + g, C, epoch, a.err, a.timeout_ns)) return;
+            if (threadIdx.x == 0) s_prob = __ldcg(a.gprob + g);
+        } else {
+            if (threadIdx.x == 0) s_prob = atomicAdd(a.queue, 1);
+        }
         __syncthreads();
         const int pb = s_prob;
         __syncthreads();
@@ -228,10 +277,9 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
         double *__restrict__ p = a.p + pb * n;
         double *__restrict__ q = a.q + pb * n;
         // r = b - A x, p = r
-        double bb = 0.0;
-        double rr = residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, bb);
-        bb = bsum(bb, red);
-        rr = bsum(rr, red);
+        double bb = 0.0, rr;
+        const double rr_own = residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, jb, je, bb);
+        if (!gsum(bb, bb) || !gsum(rr_own, rr)) return;
         const double tol2 = a.rtol * a.rtol * bb;
         int it = 0, status = PERKS_ERR_NOT_CONVERGED;
         for (int restart = 0;; ++restart) {
@@ -240,35 +288,35 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
             while (it < a.max_iter) {
                 // q = A p, <p, q>
                 double pq = 0.0;
-                for (int j0 = 0; j0 < ny; j0 += ROWS)
+                for (int j0 = jb; j0 < je; j0 += ROWS)
                     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
                         double qv[ROWS], pv[ROWS];
                         apply_column<ROWS>(fxp, fyp, dgp, p, nx, ny, i, j0, qv, pv);
 #pragma unroll
                         for (int u = 0; u < ROWS; ++u) {
                             const int j = j0 + u;
-                            if (j < ny) {
+                            if (j < je) {
                                 q[(long long)j * nx + i] = qv[u];
                                 pq = fma(pv[u], qv[u], pq);
                             }
                         }
                     }
-                pq = bsum(pq, red);
+                if (!gsum(pq, pq)) return;
                 if (!(pq > 0.0) || !isfinite(pq)) { status = PERKS_ERR_BREAKDOWN; break; }
                 const double alpha = rr / pq;
                 // x += alpha p, r -= alpha q, <r, r>
                 double rn = 0.0;
-                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * LIN) {
+                for (long long c0 = cb + threadIdx.x; c0 < ce; c0 += (long long)blockDim.x * LIN) {
                     double xv[LIN], rv[LIN], pv[LIN], qv[LIN];
 #pragma unroll
                     for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
-                        if (c < n) { xv[u] = x[c]; rv[u] = r[c]; pv[u] = p[c]; qv[u] = q[c]; }
+                        if (c < ce) { xv[u] = x[c]; rv[u] = r[c]; pv[u] = p[c]; qv[u] = q[c]; }
                     }
 #pragma unroll
                     for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
-                        if (c < n) {
+                        if (c < ce) {
                             x[c] = fma(alpha, pv[u], xv[u]);
                             const double ri = fma(-alpha, qv[u], rv[u]);
                             r[c] = ri;
@@ -276,34 +324,39 @@ __global__ void __launch_bounds__(NT, MINB) perks_poisson_cg_kernel(const __grid
                         }
                     }
                 }
-                rn = bsum(rn, red);
+                if (!gsum(rn, rn)) return;
                 const double beta = rn / rr;
                 // p = r + beta p
-                for (long long c0 = threadIdx.x; c0 < n; c0 += (long long)blockDim.x * LIN) {
+                for (long long c0 = cb + threadIdx.x; c0 < ce; c0 += (long long)blockDim.x * LIN) {
                     double rv[LIN], pv[LIN];
 #pragma unroll
                     for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
-                        if (c < n) { rv[u] = r[c]; pv[u] = p[c]; }
+                        if (c < ce) { rv[u] = r[c]; pv[u] = p[c]; }
                     }
 #pragma unroll
                     for (int u = 0; u < LIN; ++u) {
                         const long long c = c0 + (long long)u * blockDim.x;
-                        if (c < n) p[c] = fma(beta, pv[u], rv[u]);
+                        if (c < ce) p[c] = fma(beta, pv[u], rv[u]);
                     }
                 }
-                __syncthreads();
+                if (GROUP) {  // the next SpMV reads the neighbouring blocks' edge rows of p
+                    if (!grid_barrier(a.gbar + g, C, epoch, a.err, a.timeout_ns)) return;
+                } else {
+                    __syncthreads();
+                }
                 rr = rn;
                 ++it;
                 if (rr <= tol2) { converged = true; break; }
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             double bdum = 0.0;
-            rr = bsum(residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, bdum), red);
+            const double rt = residual_pass<true, ROWS>(fxp, fyp, dgp, b, x, r, p, nx, ny, jb, je, bdum);
+            if (!gsum(rt, rr)) return;
             if (rr <= tol2) { status = PERKS_OK; break; }
             if (!converged || restart >= a.max_restarts) break;
         }
-        if (threadIdx.x == 0) {
+        if (rank == 0 && threadIdx.x == 0) {
             a.iters[pb] = it;
             a.true_rel[pb] = bb > 0 ? sqrt(rr / bb) : sqrt(rr);
             a.status[pb] = status;
@@ -377,11 +430,18 @@ struct perks_poisson {
     int *queue = nullptr, *iters = nullptr, *status = nullptr;
     double *true_rel = nullptr;
     int block_threads = 512;  // 512 (one block per SM; measured faster) or 256 (two per SM)
+    int group = 1;            // blocks per problem
+    unsigned long long *gbar = nullptr;
+    int *gprob = nullptr;
+    double *gpart = nullptr;
+    DevError *err = nullptr;
+    int max_groups = 0;
 };
 
 namespace {
 void free_poisson(perks_poisson *P) {
-    void *ptrs[] = {P->fx, P->fy, P->dg, P->b, P->x, P->r, P->p, P->q, P->queue, P->iters, P->status, P->true_rel};
+    void *ptrs[] = {P->fx, P->fy, P->dg, P->b, P->x, P->r, P->p, P->q, P->queue, P->iters, P->status, P->true_rel,
+                    P->gbar, P->gprob, P->gpart, P->err};
     for (void *v : ptrs) if (v) cudaFree(v);
 }
 
@@ -391,6 +451,8 @@ PoissonArgs poisson_args(perks_poisson *P) {
     a.nx = P->nx; a.ny = P->ny; a.nprob = P->nprob; a.n = P->n;
     a.fx = P->fx; a.fy = P->fy; a.dg = P->dg; a.b = P->b; a.x = P->x; a.r = P->r; a.p = P->p; a.q = P->q;
     a.queue = P->queue; a.iters = P->iters; a.true_rel = P->true_rel; a.status = P->status;
+    a.group = P->group; a.gbar = P->gbar; a.gprob = P->gprob; a.gpart = P->gpart; a.err = P->err;
+    a.timeout_ns = P->ctx->timeout_ns;
     return a;
 }
 }  // namespace
@@ -420,6 +482,11 @@ extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int
     if (e == cudaSuccess) e = cudaMalloc(&P->iters, sizeof(int) * nprob);
     if (e == cudaSuccess) e = cudaMalloc(&P->status, sizeof(int) * nprob);
     if (e == cudaSuccess) e = cudaMalloc(&P->true_rel, sizeof(double) * nprob);
+    P->max_groups = 2 * ctx->sm_count;  // at most two blocks per SM
+    if (e == cudaSuccess) e = cudaMalloc(&P->gbar, sizeof(unsigned long long) * P->max_groups);
+    if (e == cudaSuccess) e = cudaMalloc(&P->gprob, sizeof(int) * P->max_groups);
+    if (e == cudaSuccess) e = cudaMalloc(&P->gpart, sizeof(double) * 2 * kPoiMaxGroup * P->max_groups);
+    if (e == cudaSuccess) e = cudaMalloc(&P->err, sizeof(DevError));
     if (e == cudaSuccess && !on_device) {
         e = cudaMalloc(&kd, vb);
         if (e == cudaSuccess) e = cudaMemcpy(kd, k, vb, cudaMemcpyHostToDevice);
@@ -465,7 +532,7 @@ extern "C" perks_status perks_poisson_scale_guess(perks_poisson *P, const double
     perks_status rc = use_device(P->ctx);
     if (rc) return rc;
     const int grid = std::max(1, std::min(P->nprob, P->ctx->sm_count));
-    poisson_scale_guess_kernel<512, 4><<<grid, 512, 0, (cudaStream_t)stream>>>(poisson_args(P), b, x);
+    poisson_scale_guess_kernel<512, kRows><<<grid, 512, 0, (cudaStream_t)stream>>>(poisson_args(P), b, x);
     PERKS_CUDA(P->ctx, cudaGetLastError());
     return PERKS_OK;
 }
@@ -486,13 +553,31 @@ extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, d
     a.rtol = rtol;
     a.max_iter = max_iter;
     a.max_restarts = 8;
-    const void *kern = P->block_threads == 512 ? (const void *)perks_poisson_cg_kernel<512, 1, 4, 2>
-                                               : (const void *)perks_poisson_cg_kernel<kPoiThreads, 2, 4, 2>;
+    const bool grouped = P->group > 1;
+    const void *kern;
+    if (P->block_threads == 512)
+        kern = grouped ? (const void *)perks_poisson_cg_kernel<512, 1, kRows, kLin, true>
+                       : (const void *)perks_poisson_cg_kernel<512, 1, kRows, kLin, false>;
+    else
+        kern = grouped ? (const void *)perks_poisson_cg_kernel<kPoiThreads, 2, kRows, kLin, true>
+                       : (const void *)perks_poisson_cg_kernel<kPoiThreads, 2, kRows, kLin, false>;
     int per_sm = 0;
     PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P->block_threads, 0));
-    const int grid = std::max(1, std::min(P->nprob, per_sm * ctx->sm_count));
+    if (per_sm < 1) return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "poisson_solve: kernel cannot be resident");
     void *kargs[] = {(void *)&a};
-    PERKS_CUDA(ctx, cudaLaunchKernel(kern, dim3(grid), dim3(P->block_threads), kargs, 0, s));
+    int grid;
+    if (!grouped) {
+        grid = std::max(1, std::min(P->nprob, per_sm * ctx->sm_count));
+        PERKS_CUDA(ctx, cudaLaunchKernel(kern, dim3(grid), dim3(P->block_threads), kargs, 0, s));
+    } else {
+        // groups wait on one another's blocks: every block resident (cooperative launch)
+        const int groups = std::min({P->nprob, per_sm * ctx->sm_count / P->group, P->max_groups});
+        if (groups < 1) return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "poisson_solve: group larger than the GPU");
+        grid = groups * P->group;
+        PERKS_CUDA(ctx, cudaMemsetAsync(P->gbar, 0, sizeof(unsigned long long) * groups, s));
+        PERKS_CUDA(ctx, cudaMemsetAsync(P->err, 0, sizeof(DevError), s));
+        PERKS_CUDA(ctx, cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(P->block_threads), kargs, 0, s));
+    }
     PERKS_CUDA(ctx, cudaMemcpyAsync(x, P->x, vb, cudaMemcpyDeviceToDevice, s));
     if (!stats) return PERKS_OK;
     PERKS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -527,7 +612,21 @@ extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, d
     delete[] it;
     delete[] st;
     delete[] tr;
+    if (grouped) {
+        DevError de{};
+        PERKS_CUDA(ctx, cudaMemcpy(&de, P->err, sizeof(DevError), cudaMemcpyDeviceToHost));
+        if (de.code != 0)
+            return fail(ctx, de.code, "poisson_solve: a block group's barrier gave up (block %d)", de.block);
+    }
     if (worst != PERKS_OK) return fail(ctx, worst, "poisson_solve: a problem did not converge (status %d)", worst);
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_set_group(perks_poisson *P, int32_t blocks) {
+    if (!P) return PERKS_ERR_INVALID_ARG;
+    if (blocks != 1 && blocks != 2 && blocks != 4 && blocks != 8)
+        return fail(P->ctx, PERKS_ERR_INVALID_ARG, "poisson_set_group: 1, 2, 4 or 8 blocks per problem");
+    P->group = blocks;
     return PERKS_OK;
 }
 

@@ -113,3 +113,50 @@ def test_scale_guess_matches_oracle(ctx, oracle):
                 return oracle.dot(e, oracle.spmv(rp, c, val, e))
             assert anorm(u - xs[i].ravel()) <= anorm(u - x[i].ravel())
     assert not xs[3].any()
+
+
+@pytest.mark.parametrize("group", [2, 4, 8])
+@pytest.mark.parametrize("nprob,ny,nx", [(5, 24, 31), (40, 37, 16)])
+def test_block_groups_match_oracle(ctx, oracle, group, nprob, ny, nx):
+    """Rows of each problem split over a group of blocks (37 rows over 8
+    blocks leaves some blocks one row block or none): every problem reaches
+    the tolerance and agrees with the oracle's CG."""
+    from paper_2204_02064_gb300 import api
+    k = _k(nprob, ny, nx, 11)
+    f = 2.0 * inputs.uniform(12, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    P.set_group(group)
+    x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    res = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
+    xs = x.cpu().numpy()
+    assert res["max_true_rel_residual"] <= 1e-8
+    assert res["grid_blocks"] % group == 0
+    for i in range(0, nprob, max(1, nprob // 5)):
+        rp, c, val = oracle.poisson_csr(k[i])
+        ref = oracle.cg(rp, c, val, f[i].ravel(), rtol=1e-8, max_iter=20000)
+        assert abs(int(res["iterations"][i]) - ref["iters"]) <= 2
+        assert np.linalg.norm(xs[i].ravel() - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+
+
+def test_block_group_barrier_timeout_reported(ctx):
+    """A group barrier that gives up at its first wait (timeout 0) ends the
+    solve with BARRIER_TIMEOUT; the context stays usable."""
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 6, 32, 32
+    k = _k(nprob, ny, nx, 13)
+    f = torch.from_numpy(2.0 * inputs.uniform(14, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0).cuda()
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    P.set_group(2)
+    x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    ctx.set_barrier_timeout(0)
+    try:
+        with pytest.raises(api.PerksError) as ei:
+            P.solve(f, x, rtol=1e-8)
+        assert ei.value.name == "BARRIER_TIMEOUT"
+    finally:
+        ctx.set_barrier_timeout(2_000_000_000)
+    x.zero_()
+    assert P.solve(f, x, rtol=1e-8)["max_true_rel_residual"] <= 1e-8
+    with pytest.raises(api.PerksError) as ei:
+        P.set_group(3)
+    assert ei.value.name == "INVALID_ARG"
