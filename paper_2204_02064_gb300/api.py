@@ -608,7 +608,7 @@ class Poisson:
         self.ctx.check(self._lib.perks_poisson_set_block_threads(self.handle, int(threads)))
 
     def set_group(self, blocks: int):
-        """Blocks per problem: 1 (default), 2, 4 or 8 (rows split over the group)."""
+        """Blocks per problem: 0 (automatic, default), 1, 2, 4 or 8 (rows split over the group)."""
         self.ctx.check(self._lib.perks_poisson_set_group(self.handle, int(blocks)))
 
     def solve(self, b, x, rtol: float = 1e-8, max_iter: int = 20000, stream=None, stats: bool = True):

@@ -334,6 +334,27 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     }
     bp.cached_cells = cached;
     bp.halo_cells = halo;
+    if (!st->has_plan && !per_step && cached < st->cells) {
+        // Default plan when the caches cannot hold the whole domain: the
+        // cache-free body for all steps in one launch.  Measured on GB300,
+        // caching a part of a domain (3-D 384^3 in fp64/fp32/bf16, 2-D 4096^2)
+        // costs more in bookkeeping than the re-reads it saves.
+        const perks_stencil_plan saved_plan = st->plan;
+        const std::string saved_msg = ctx->last_error;
+        st->has_plan = true;
+        st->plan = perks_stencil_plan{};
+        st->plan.reg_cache = 0;
+        st->plan.smem_cache_planes = 0;
+        Plan cf;
+        const perks_status r2 = make_plan(st, cf, false);
+        st->has_plan = false;
+        st->plan = saved_plan;
+        if (r2 == PERKS_OK) {
+            pl = cf;
+            return PERKS_OK;
+        }
+        ctx->last_error = saved_msg;  // no cache-free plan: keep the cached one
+    }
     pl = bp;
     return PERKS_OK;
 }

@@ -160,3 +160,19 @@ def test_block_group_barrier_timeout_reported(ctx):
     with pytest.raises(api.PerksError) as ei:
         P.set_group(3)
     assert ei.value.name == "INVALID_ARG"
+
+
+def test_automatic_block_groups(ctx):
+    """By default problems of 64K cells and more get groups of 4 blocks,
+    smaller ones one block each."""
+    from paper_2204_02064_gb300 import api
+    for ny, nx, per in ((256, 256, 4), (64, 64, 1)):
+        nprob = 3
+        k = _k(nprob, ny, nx, 15)
+        f = torch.from_numpy(2.0 * inputs.uniform(16, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0).cuda()
+        P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+        x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+        res = P.solve(f, x, rtol=1e-8)
+        assert res["grid_blocks"] == nprob * per
+        assert res["max_true_rel_residual"] <= 1e-8
+        P.close()

@@ -424,3 +424,23 @@ def test_high_order_2d_stars_unaligned_extent(ctx, oracle, name, shape):
     with pytest.raises(api.PerksError) as ei:
         _run_gpu(ctx, name, f, 7, dtype="f32", variant=0)
     assert ei.value.name == "UNSUPPORTED"
+
+
+def test_default_plan_caches_whole_domains_only(ctx, oracle):
+    """Without a plan, a domain the on-chip caches hold whole is cached; a
+    larger one runs the cache-free body for all steps in one launch (and
+    still matches the oracle)."""
+    from paper_2204_02064_gb300 import api
+    small = api.Stencil(ctx, (256, 256), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"))
+    d = small.describe(10, api.PERSISTENT)
+    assert d["cached_cells"] == d["cells"]
+    small.close()
+    big = api.Stencil(ctx, (4096, 4096), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"),
+                      dtype="f32")
+    d = big.describe(10, api.PERSISTENT)
+    assert d["cached_cells"] == 0 and d["reg_cache_planes"] == 0 and d["smem_cache_planes"] == 0
+    big.close()
+    f = inputs.stencil_field((2900, 2048), 17)  # 23.8 MB of fp32: more than the caches hold
+    out, stats = _run_gpu(ctx, "2d5pt", f, 6, dtype="f32")
+    assert stats["cached_cells"] in (0, stats["cells"])
+    assert rel_err(out, _oracle(oracle, "2d5pt", f, 6)) <= TOL["f32"]
