@@ -72,6 +72,9 @@ typedef void *perks_stream; /* cudaStream_t */
  * perks_context_destroy.  Errors: INVALID_ARG (out NULL or bad device),
  * CUDA. */
 perks_status perks_context_create(int device, perks_context **out);
+/* Frees the context.  Objects created on it may still be destroyed
+ * afterwards (their destroy calls do not touch the context); every other
+ * call on them needs the context alive. */
 perks_status perks_context_destroy(perks_context *ctx);
 
 /* Message of the last failed call on this context (or on an object made

@@ -174,6 +174,7 @@ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 struct perks_batch {
     perks_context *ctx = nullptr;
+    int device = 0;  // for destroy, which may come after the context is gone
     int dtype = PERKS_F32;
     int es = 4;
     int ndom = 0;
@@ -485,6 +486,7 @@ extern "C" perks_status perks_batch_create(perks_context *ctx, int32_t ndom, con
     const int dtype = descs[0].dtype;
     auto *b = new perks_batch();
     b->ctx = ctx;
+    b->device = ctx->device;
     b->dtype = dtype;
     b->es = (int)dtype_size(dtype);
     b->ndom = ndom;
@@ -528,7 +530,7 @@ extern "C" perks_status perks_batch_create(perks_context *ctx, int32_t ndom, con
 
 extern "C" perks_status perks_batch_destroy(perks_batch *b) {
     if (!b) return PERKS_OK;
-    if (b->ctx) cudaSetDevice(b->ctx->device);
+    cudaSetDevice(b->device);
     for (int p = 0; p < 2; ++p) {
         for (void *q : b->field[p]) if (q) cudaFree(q);
         for (void *q : b->faces[p]) if (q) cudaFree(q);

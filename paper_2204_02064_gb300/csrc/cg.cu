@@ -278,6 +278,7 @@ __global__ void seg_tiles_kernel(const unsigned *cnt, long long ntiles, unsigned
 
 struct perks_op {
     perks_context *ctx = nullptr;
+    int device = 0;  // for destroy, which may come after the context is gone
     int n = 0;
     long long nnz = 0;
     int G = 0;
@@ -598,6 +599,7 @@ extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t 
     if (rc) return rc;
     perks_op *op = new perks_op();
     op->ctx = ctx;
+    op->device = ctx->device;
     op->n = n;
     op->nnz = nnz;
     op->G = ctx->sm_count;
@@ -704,7 +706,7 @@ extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t 
 
 extern "C" perks_status perks_op_destroy(perks_op *op) {
     if (!op) return PERKS_OK;
-    if (op->ctx) cudaSetDevice(op->ctx->device);
+    cudaSetDevice(op->device);
     free_op(op);
     delete op;
     return PERKS_OK;

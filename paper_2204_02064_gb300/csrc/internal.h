@@ -48,8 +48,12 @@ inline perks_status cuda_fail(perks_context *ctx, cudaError_t e, const char *wha
     } while (0)
 
 // Sets the context's device current for the calling thread.
+// Makes the context's device current and clears the runtime's last-error
+// slot, so the launch checks of this call report this call's launches only
+// (not an error some earlier, unrelated runtime call left behind).
 inline perks_status use_device(perks_context *ctx) {
     PERKS_CUDA(ctx, cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();
     return PERKS_OK;
 }
 

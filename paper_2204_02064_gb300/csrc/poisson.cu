@@ -423,6 +423,7 @@ __global__ void poisson_apply_kernel(const __grid_constant__ PoissonArgs a, cons
 
 struct perks_poisson {
     perks_context *ctx = nullptr;
+    int device = 0;  // for destroy, which may come after the context is gone
     int nx = 0, ny = 0, nprob = 0;
     long long n = 0;
     double *fx = nullptr, *fy = nullptr, *dg = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr,
@@ -476,6 +477,7 @@ extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int
     if (rc) return rc;
     auto *P = new perks_poisson();
     P->ctx = ctx;
+    P->device = ctx->device;
     P->nx = nx; P->ny = ny; P->nprob = nprob;
     P->n = (long long)nx * ny;
     const size_t vb = sizeof(double) * (size_t)P->n * nprob;
@@ -518,7 +520,7 @@ extern "C" perks_status perks_poisson_create(perks_context *ctx, int32_t nx, int
 
 extern "C" perks_status perks_poisson_destroy(perks_poisson *P) {
     if (!P) return PERKS_OK;
-    if (P->ctx) cudaSetDevice(P->ctx->device);
+    cudaSetDevice(P->device);
     free_poisson(P);
     delete P;
     return PERKS_OK;

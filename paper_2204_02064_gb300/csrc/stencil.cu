@@ -152,6 +152,7 @@ struct Plan {
 
 struct perks_stencil {
     perks_context *ctx = nullptr;
+    int device = 0;  // for destroy, which may come after the context is gone
     perks_stencil_desc desc{};
     int es = 8;
     int X = 0, Y = 0, Z = 0;         // internal orientation (persistent kernel)
@@ -554,6 +555,7 @@ extern "C" perks_status perks_stencil_create(perks_context *ctx, const perks_ste
     if (rc) return rc;
     perks_stencil *st = new perks_stencil();
     st->ctx = ctx;
+    st->device = ctx->device;
     st->desc = *d;
     st->es = (int)dtype_size(d->dtype);
     st->uX = (int)d->nx; st->uY = (int)d->ny; st->uZ = (int)d->nz;
@@ -575,7 +577,7 @@ extern "C" perks_status perks_stencil_create(perks_context *ctx, const perks_ste
 
 extern "C" perks_status perks_stencil_destroy(perks_stencil *st) {
     if (!st) return PERKS_OK;
-    if (st->ctx) cudaSetDevice(st->ctx->device);
+    cudaSetDevice(st->device);
     for (int i = 0; i < 2; ++i) {
         if (st->field[i]) cudaFree(st->field[i]);
         if (st->faces[i]) cudaFree(st->faces[i]);

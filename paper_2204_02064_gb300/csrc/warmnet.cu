@@ -282,6 +282,7 @@ template <typename K> perks_status set_smem(perks_context *ctx, K kernel, size_t
 
 struct perks_warmnet {
     perks_context *ctx = nullptr;
+    int device = 0;  // for destroy, which may come after the context is gone
     int C = kMaxC;
     int dil[4] = {1, 2, 4, 8};
     int storage = PERKS_BF16;
@@ -489,6 +490,7 @@ extern "C" perks_status perks_warmnet_create(perks_context *ctx, const int32_t *
     if (rc) return rc;
     auto *n = new perks_warmnet();
     n->ctx = ctx;
+    n->device = ctx->device;
     n->storage = storage;
     if (dilations)
         for (int l = 0; l < 4; ++l) {
@@ -527,7 +529,7 @@ extern "C" perks_status perks_warmnet_create(perks_context *ctx, const int32_t *
 
 extern "C" perks_status perks_warmnet_destroy(perks_warmnet *n) {
     if (!n) return PERKS_OK;
-    if (n->ctx) cudaSetDevice(n->ctx->device);
+    cudaSetDevice(n->device);
     free_net_bufs(n);
     void *p[] = {n->params, n->grads, n->m, n->v, n->loss, n->ut, n->err};
     for (void *q : p) if (q) cudaFree(q);

@@ -113,6 +113,7 @@ def test_scale_guess_matches_oracle(ctx, oracle):
                 return oracle.dot(e, oracle.spmv(rp, c, val, e))
             assert anorm(u - xs[i].ravel()) <= anorm(u - x[i].ravel())
     assert not xs[3].any()
+    P.close()
 
 
 @pytest.mark.parametrize("group", [2, 4, 8])
@@ -136,6 +137,7 @@ def test_block_groups_match_oracle(ctx, oracle, group, nprob, ny, nx):
         ref = oracle.cg(rp, c, val, f[i].ravel(), rtol=1e-8, max_iter=20000)
         assert abs(int(res["iterations"][i]) - ref["iters"]) <= 2
         assert np.linalg.norm(xs[i].ravel() - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    P.close()
 
 
 def test_block_group_barrier_timeout_reported(ctx):
@@ -160,6 +162,7 @@ def test_block_group_barrier_timeout_reported(ctx):
     with pytest.raises(api.PerksError) as ei:
         P.set_group(3)
     assert ei.value.name == "INVALID_ARG"
+    P.close()
 
 
 def test_automatic_block_groups(ctx):

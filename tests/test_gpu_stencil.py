@@ -444,3 +444,18 @@ def test_default_plan_caches_whole_domains_only(ctx, oracle):
     out, stats = _run_gpu(ctx, "2d5pt", f, 6, dtype="f32")
     assert stats["cached_cells"] in (0, stats["cells"])
     assert rel_err(out, _oracle(oracle, "2d5pt", f, 6)) <= TOL["f32"]
+
+
+def test_objects_destroyed_after_their_context(ctx):
+    """Destroying a stencil and a Poisson batch after their context is gone
+    touches nothing of the context, and the next call elsewhere sees no stale
+    CUDA error."""
+    from paper_2204_02064_gb300 import api
+    c2 = api.Context(0)
+    st = api.Stencil(c2, (16, 16), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"))
+    P = api.Poisson(c2, torch.ones(1, 8, 8, dtype=torch.float64, device="cuda"))
+    c2.close()
+    st.close()
+    P.close()
+    f = inputs.stencil_field((21, 19, 23), 8)
+    out, _ = _run_gpu(ctx, "3d7pt", f, 5, variant=1)
