@@ -126,6 +126,8 @@ def _declare(lib):
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_op_set_spmv": ([P, i32], i32),
+        "perks_op_set_vector_cache": ([P, i32], i32),
+        "perks_op_vector_cache_active": ([P], i32),
         "perks_stencil_set_trace": ([P, i32], i32),
         "perks_stencil_autotune": ([P, i32, i32, P, ctypes.POINTER(StencilPlan), ctypes.POINTER(f64)], i32),
         "perks_stencil_get_trace": ([P, P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -455,6 +457,15 @@ class CsrOperator:
         SPMV_SEG (vector and nonzeros staged in shared memory one column
         segment at a time; its layout is built on first selection)."""
         self.ctx.check(self._lib.perks_op_set_spmv(self.handle, int(kind)))
+
+    def set_vector_cache(self, on: bool):
+        """Keep each block's rows of x, r, q (fp32 inner: r, d, q) in shared
+        memory during a persistent solve with SPMV_ROWVEC (default on)."""
+        self.ctx.check(self._lib.perks_op_set_vector_cache(self.handle, 1 if on else 0))
+
+    @property
+    def vector_cache_active(self) -> bool:
+        return bool(self._lib.perks_op_vector_cache_active(self.handle))
 
     def spmv(self, x, y, stream=None):
         xp, xd, _ = _buffer(x)

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) cg_multi_spmv(const __grid_cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const CgSmem s = carve_cg_smem(smem_raw);
     const CgSlice sl = load_slice(a, s);
-    const double d = spmv_any<double>(a, s, sl, a.val, v, q, dotv);
+    const double d = spmv_any<double>(a, s, sl, a.val, v, q, dotv, nullptr);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = d;
 }
 
@@ -289,6 +289,10 @@ struct perks_op {
     int2 *part_tiles = nullptr;
     int G2 = 0;                                         // row-vector kernel: G2 blocks
     int *part_row2 = nullptr, *part_ntiles2 = nullptr;
+    int max_rows2 = 0;                                  // rows of the largest row-vector block
+    size_t smem_vc = 0;                                 // row-vector kernel's shared memory with the vector cache
+    bool vcache_ok = false;                             // the cache fits with G2 blocks co-resident
+    bool vcache_on = true;                              // perks_op_set_vector_cache
     int2 *part_tiles2 = nullptr;
     // column-segmented SpMV: G blocks (part_row), layout built on first use
     bool seg_built = false;
@@ -361,6 +365,8 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.mode = mode;
     a.allow_cache = 1;
     a.spmv_kind = op->spmv_kind;
+    a.vcache = rv && op->vcache_ok && op->vcache_on && mode != CGK_SPMV;
+    a.vcache_rows = op->max_rows2;
     a.seg.nseg = op->nseg;
     a.seg.val = op->sval;
     a.seg.val32 = op->sval32;
@@ -396,6 +402,20 @@ perks_status configure(perks_op *op) {
                                                                   kCgThreads, kCgRowvecSmem));
     if (per_sm2 < 1 || per_sm2 * ctx->sm_count < op->G2)
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "CG kernel of %d blocks is not co-resident", op->G2);
+    // vector cache: on when the largest block's rows fit with all G2 blocks co-resident
+    op->smem_vc = kCgRowvecSmem + (((size_t)op->max_rows2 * kCgVcacheBytesPerRow + 15) & ~size_t(15));
+    op->vcache_ok = false;
+    // (the attribute is per function, shared by every operator: set to the
+    // device limit; each launch passes its own size)
+    if (op->smem_vc <= (size_t)ctx->smem_optin &&
+        cudaFuncSetAttribute((const void *)perks_cg_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ctx->smem_optin) == cudaSuccess) {
+        int per_vc = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_vc, (const void *)perks_cg_kernel<0>, kCgThreads,
+                                                          op->smem_vc) == cudaSuccess)
+            op->vcache_ok = per_vc * ctx->sm_count >= op->G2;
+    }
+    (void)cudaGetLastError();
     int per_sm3 = 0;
     PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, (const void *)perks_cg_kernel<2>,
                                                                   kCgThreads, seg_smem_bytes()));
@@ -412,7 +432,8 @@ perks_status launch_persistent(perks_op *op, const CgArgs &a, cudaStream_t s) {
     void *args[] = {(void *)&a};
     if (op->spmv_kind == PERKS_SPMV_ROWVEC)
         PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<0>, dim3(op->G2),
-                                                    dim3(kCgThreads), args, kCgRowvecSmem, s));
+                                                    dim3(kCgThreads), args,
+                                                    a.vcache ? op->smem_vc : kCgRowvecSmem, s));
     else if (op->spmv_kind == PERKS_SPMV_SEG)
         PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<2>, dim3(op->G),
                                                     dim3(kCgThreads), args, seg_smem_bytes(), s));
@@ -485,8 +506,12 @@ perks_status read_result(perks_op *op, cudaStream_t s, perks_cg_stats *stats) {
         const double vbytes = op->last_mode == PERKS_CG_FP32_IR ? 4.0 : 8.0;
         // A (values + column indices + row pointers) once, the gathered vector
         // once, and the vector updates: q, x, r, p read/written per iteration.
+        // With the vector cache, x (d), r and q stay on chip: p's gather,
+        // its read in the update and its read and write in the direction remain.
+        const bool vc = op->spmv_kind == PERKS_SPMV_ROWVEC && op->vcache_ok && op->vcache_on;
         stats->bytes_per_iteration = op->nnz * (vbytes + 4.0) + 4.0 * (op->n + 1.0) +
-                                     vbytes * op->n * (1.0 + 1.0 + 2.0 + 2.0 + 2.0 + 2.0);
+                                     vbytes * op->n * (vc ? 1.0 + 1.0 + 2.0
+                                                          : 1.0 + 1.0 + 2.0 + 2.0 + 2.0 + 2.0);
         if (stats->trace && stats->trace_len > 0) {
             const int k = std::min(std::min(stats->trace_len, op->trace_cap), r.iterations);
             if (k > 0)
@@ -670,6 +695,11 @@ extern "C" perks_status perks_csr_create(perks_context *ctx, int32_t n, int64_t 
     cg_partition_kernel<<<G2, 256>>>(op->rowptr, n, nnz, G2, op->part_row2, op->part_ntiles2, op->part_tiles2,
                                      overflow);
     OPCUDA(cudaGetLastError());
+    {
+        std::vector<int> pr((size_t)G2 + 1);
+        OPCUDA(cudaMemcpy(pr.data(), op->part_row2, sizeof(int) * ((size_t)G2 + 1), cudaMemcpyDeviceToHost));
+        for (int g = 0; g < G2; ++g) op->max_rows2 = std::max(op->max_rows2, pr[g + 1] - pr[g]);
+    }
     int ov = 0;
     OPCUDA(cudaMemcpy(&ov, overflow, sizeof(int), cudaMemcpyDeviceToHost));
     cudaFree(overflow);
@@ -775,6 +805,17 @@ extern "C" perks_status perks_cg_last_result(perks_op *op, perks_stream stream, 
     if (rc) return rc;
     perks_cg_stats local{};
     return read_result(op, (cudaStream_t)stream, stats ? stats : &local);
+}
+
+extern "C" perks_status perks_op_set_vector_cache(perks_op *op, int32_t on) {
+    if (!op) return PERKS_ERR_INVALID_ARG;
+    if (on != 0 && on != 1) return fail(op->ctx, PERKS_ERR_INVALID_ARG, "op_set_vector_cache: 0 or 1");
+    op->vcache_on = on != 0;
+    return PERKS_OK;
+}
+
+extern "C" int32_t perks_op_vector_cache_active(const perks_op *op) {
+    return op && op->vcache_ok && op->vcache_on && op->spmv_kind == PERKS_SPMV_ROWVEC ? 1 : 0;
 }
 
 extern "C" perks_status perks_op_set_spmv(perks_op *op, int32_t kind) {

@@ -74,6 +74,8 @@ struct CgArgs {
     int mode;
     int allow_cache;
     int spmv_kind;           // 0: row-vector SpMV (default), 1: thread-level merge walk, 2: column-segmented
+    int vcache;              // row-vector kind: the block's rows of x, r, q (fp64) or r32, d32, q32 in shared memory
+    int vcache_rows;         // rows of the largest block (capacity of each cached vector)
     const double *spmv_in;
     double *spmv_out;
     SegArgs seg;             // column-segmented layout (spmv_kind 2)
@@ -365,7 +367,8 @@ constexpr int kRowsPer = 4;
 
 template <typename V>
 __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__restrict__ gval,
-                                 const V *__restrict__ vin, V *__restrict__ vout, const V *dotv, double *red) {
+                                 const V *__restrict__ vin, V *__restrict__ vout, const V *dotv, double *red,
+                                 V *vout_s) {
     const int lane = threadIdx.x & (kSub - 1);
     const int sub = threadIdx.x / kSub;
     const int nsub = blockDim.x / kSub;
@@ -402,7 +405,8 @@ __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__
             for (int k = 0; k < kRowsPer; ++k) {
                 const int r = row0 + k;
                 if (r < sl.r1) {
-                    vout[r] = acc[k];
+                    if (vout_s) vout_s[r - sl.r0] = acc[k];  // the block's own rows, kept on chip
+                    else vout[r] = acc[k];
                     if (dotv) dot = fma((double)dotv[r], (double)acc[k], dot);
                 }
             }
@@ -414,8 +418,8 @@ __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__
 
 template <typename V>
 __device__ __forceinline__ double spmv_any(const CgArgs &a, const CgSmem &s, const CgSlice &sl, const V *gval,
-                                           const V *vin, V *vout, const V *dotv) {
-    if (a.spmv_kind == 0 && !sl.cached) return spmv_block_vec<V>(a, sl, gval, vin, vout, dotv, s.red);
+                                           const V *vin, V *vout, const V *dotv, V *vout_s) {
+    if (a.spmv_kind == 0 && !sl.cached) return spmv_block_vec<V>(a, sl, gval, vin, vout, dotv, s.red, vout_s);
     if (s.bufs == nullptr) return 0.0;  // row-vector kernel: never reached (spmv_kind is 0)
     return spmv_block<V>(a, s, sl, gval, vin, vout, dotv);
 }
@@ -425,15 +429,18 @@ template <> __device__ __forceinline__ const double *seg_vals<double>(const SegA
 template <> __device__ __forceinline__ const float *seg_vals<float>(const SegArgs &g) { return g.val32; }
 
 // The SpMV of kernel kind KIND (0 row-vector, 1 merge walk, 2 column-segmented).
+// vout_s (row-vector kind only): the block's rows of the result go there,
+// indexed from the block's first row, instead of to vout.
 template <int KIND, typename V>
 __device__ __forceinline__ double spmv_k(const CgArgs &a, const CgSmem &s, const CgSlice &sl, const V *gval,
-                                         const V *vin, V *vout, const V *dotv, unsigned char *smem, SegState &st) {
+                                         const V *vin, V *vout, const V *dotv, unsigned char *smem, SegState &st,
+                                         V *vout_s = nullptr) {
     if constexpr (KIND == 2) {
         bool ok;
         return spmv_seg<V>(a.seg, a.n, sl.r0, sl.r1, seg_vals<V>(a.seg), vin, vout, dotv, smem, st, s.red, a.err,
                            a.timeout_ns, ok);
     } else {
-        return spmv_any<V>(a, s, sl, gval, vin, vout, dotv);
+        return spmv_any<V>(a, s, sl, gval, vin, vout, dotv, KIND == 0 ? vout_s : nullptr);
     }
 }
 
@@ -441,8 +448,11 @@ __device__ __forceinline__ bool cg_sync(const CgArgs &a, unsigned long long &epo
     return grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns);
 }
 
-// Shared memory of the row-vector kernel: the reduction scratch only.
+// Shared memory of the row-vector kernel: the reduction scratch, followed
+// (vector cache on) by kCgVcacheBytesPerRow bytes per row of the largest
+// block: x, r and q in fp64, or r32, d32 and q32 for the fp32 inner solves.
 constexpr size_t kCgRowvecSmem = 1024;
+constexpr size_t kCgVcacheBytesPerRow = 3 * sizeof(double);
 
 // Persistent CG (mode FP64 / FP32_IR) or a single SpMV (mode SPMV).
 // ROWVEC: row-vector SpMV only, 1 KB of shared memory and at most 64
@@ -501,12 +511,36 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
     const double *b = a.b;
     double *x = a.x, *r = a.r, *p = a.p, *q = a.q;
 
+    // Vector cache (row-vector kind; the paper's caching of r, Sec. 4.3.2):
+    // the vectors only this block touches -- x, r, q in fp64, r32, d32, q32
+    // in the fp32 inner solves -- stay in shared memory for the whole solve;
+    // p (p32), gathered by every block, stays in global memory.  x goes back
+    // to global memory before each true-residual SpMV (which gathers it) and
+    // at the end.
+    const bool vc64 = KIND == 0 && a.vcache && a.mode == CGK_FP64;
+    const bool vc32 = KIND == 0 && a.vcache && a.mode == CGK_FP32_IR;
+    const int cap = a.vcache_rows;
+    double *xs = reinterpret_cast<double *>(smem_raw + kCgRowvecSmem);
+    double *rs = xs + cap, *qs = rs + cap;
+    float *r32s = reinterpret_cast<float *>(smem_raw + kCgRowvecSmem);
+    float *d32s = r32s + cap, *q32s = d32s + cap;
+    const int r0 = sl.r0;
+    auto X = [&](int i) -> double & { return vc64 ? xs[i - r0] : x[i]; };
+    auto R = [&](int i) -> double & { return vc64 ? rs[i - r0] : r[i]; };
+    auto Q = [&](int i) -> double & { return vc64 ? qs[i - r0] : q[i]; };
+    auto put_x = [&]() {  // cached x -> global x (own rows)
+        if (vc64)
+            for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) x[i] = xs[i - r0];
+    };
+
     // ---- r0 = b - A x0, ||b||^2
-    spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);
+    if (vc64)
+        for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) xs[i - r0] = x[i];
+    spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st, vc64 ? qs : nullptr);
     double bb_p = 0.0, rr_p = 0.0;
     for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
-        const double ri = b[i] - q[i];
-        r[i] = ri;
+        const double ri = b[i] - Q(i);
+        R(i) = ri;
         p[i] = ri;
         bb_p += b[i] * b[i];
         rr_p += ri * ri;
@@ -529,7 +563,7 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
             bool converged = false;
             while (it < a.max_iter) {
                 // A: q = A p, <p, q>
-                const double pq_p = spmv_k<KIND, double>(a, s, sl, a.val, p, q, p, smem_raw, st);
+                const double pq_p = spmv_k<KIND, double>(a, s, sl, a.val, p, q, p, smem_raw, st, vc64 ? qs : nullptr);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 // B: alpha; x += alpha p; r -= alpha q; <r, r>
@@ -538,9 +572,9 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
                 const double alpha = rr / pq;
                 double rn_p = 0.0;
                 for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
-                    x[i] = fma(alpha, p[i], x[i]);
-                    const double ri = fma(-alpha, q[i], r[i]);
-                    r[i] = ri;
+                    X(i) = fma(alpha, p[i], X(i));
+                    const double ri = fma(-alpha, Q(i), R(i));
+                    R(i) = ri;
                     rn_p += ri * ri;
                 }
                 rn_p = block_sum(rn_p, s.red);
@@ -554,19 +588,23 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
                     a.trace[3 * it + 1] = beta;
                     a.trace[3 * it + 2] = rr_new;
                 }
-                for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p[i] = fma(beta, p[i], r[i]);
+                for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p[i] = fma(beta, p[i], R(i));
                 rr = rr_new;
                 ++it;
                 if (!cg_sync(a, epoch)) return;
                 if (rr <= tol2) { converged = true; break; }
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
-            // C5: true residual in fp64
-            spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);
+            // C5: true residual in fp64 (the SpMV gathers x from global memory)
+            if (vc64) {
+                put_x();
+                if (!cg_sync(a, epoch)) return;
+            }
+            spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st, vc64 ? qs : nullptr);
             double tr_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
-                const double ri = b[i] - q[i];
-                r[i] = ri;
+                const double ri = b[i] - Q(i);
+                R(i) = ri;
                 tr_p += ri * ri;
             }
             tr_p = block_sum(tr_p, s.red);
@@ -575,12 +613,16 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
             rr = grid_sum(part0, G, s.red);
             if (rr <= tol2) { status = PERKS_OK; break; }
             if (!converged || restart >= a.max_restarts) break;
-            for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p[i] = r[i];
+            for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p[i] = R(i);
             ++outer;
             if (!cg_sync(a, epoch)) return;
         }
+        put_x();
     } else {  // CGK_FP32_IR
         float *r32 = a.r32, *p32 = a.p32, *q32 = a.q32, *d32 = a.d32;
+        auto R32 = [&](int i) -> float & { return vc32 ? r32s[i - r0] : r32[i]; };
+        auto D32 = [&](int i) -> float & { return vc32 ? d32s[i - r0] : d32[i]; };
+        auto Q32 = [&](int i) -> float & { return vc32 ? q32s[i - r0] : q32[i]; };
         for (;;) {
             // outer: rr holds ||b - A x||^2 (fp64); r holds the residual
             if (rr <= tol2) { status = PERKS_OK; break; }
@@ -588,9 +630,9 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
             double r0_p = 0.0;
             for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
                 const float ri = (float)r[i];
-                r32[i] = ri;
+                R32(i) = ri;
                 p32[i] = ri;
-                d32[i] = 0.0f;
+                D32(i) = 0.0f;
                 r0_p += (double)ri * (double)ri;
             }
             r0_p = block_sum(r0_p, s.red);
@@ -600,7 +642,8 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
             const double itol2 = a.inner_rtol * a.inner_rtol * irr;
             if (!cg_sync(a, epoch)) return;
             while (it < a.max_iter) {
-                const double pq_p = spmv_k<KIND, float>(a, s, sl, a.val32, p32, q32, p32, smem_raw, st);
+                const double pq_p =
+                    spmv_k<KIND, float>(a, s, sl, a.val32, p32, q32, p32, smem_raw, st, vc32 ? q32s : nullptr);
                 if (tid == 0) part0[blk] = pq_p;
                 if (!cg_sync(a, epoch)) return;
                 const double pq = grid_sum(part0, G, s.red);
@@ -608,9 +651,9 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
                 const float alpha = (float)(irr / pq);
                 double rn_p = 0.0;
                 for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) {
-                    d32[i] = fmaf(alpha, p32[i], d32[i]);
-                    const float ri = fmaf(-alpha, q32[i], r32[i]);
-                    r32[i] = ri;
+                    D32(i) = fmaf(alpha, p32[i], D32(i));
+                    const float ri = fmaf(-alpha, Q32(i), R32(i));
+                    R32(i) = ri;
                     rn_p += (double)ri * (double)ri;
                 }
                 rn_p = block_sum(rn_p, s.red);
@@ -618,7 +661,7 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
                 if (!cg_sync(a, epoch)) return;
                 const double rr_new = grid_sum(part1, G, s.red);
                 const float beta = (float)(rr_new / irr);
-                for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p32[i] = fmaf(beta, p32[i], r32[i]);
+                for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) p32[i] = fmaf(beta, p32[i], R32(i));
                 irr = rr_new;
                 ++it;
                 if (!cg_sync(a, epoch)) return;
@@ -626,7 +669,7 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
             }
             if (status == PERKS_ERR_BREAKDOWN) break;
             // x += d (fp64), then the fp64 residual of the refined x
-            for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) x[i] += (double)d32[i];
+            for (int i = sl.r0 + tid; i < sl.r1; i += blockDim.x) x[i] += (double)D32(i);
             ++outer;
             if (!cg_sync(a, epoch)) return;
             spmv_k<KIND, double>(a, s, sl, a.val, x, q, nullptr, smem_raw, st);

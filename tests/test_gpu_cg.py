@@ -260,3 +260,44 @@ def test_cg_nan_rhs_reports_breakdown(ctx):
     with pytest.raises(api.PerksError) as ei:
         _solve(ctx, rp, c, v, b, 0)
     assert ei.value.name in ("BREAKDOWN", "NOT_CONVERGED")
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "fp32_ir"])
+def test_vector_cache_on_off_identical(ctx, oracle, system_4k, mode):
+    """The vector cache (each block's rows of x, r, q -- or the inner r, d, q
+    -- in shared memory) changes where values live, not the arithmetic: the
+    solutions and iteration counts are identical with it on and off."""
+    rp, c, v, b = system_4k
+    out = {}
+    for on in (True, False):
+        op = _op(ctx, rp, c, v)
+        op.set_vector_cache(on)
+        assert op.vector_cache_active == on
+        x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        res = op.solve(_dev(b), x, rtol=1e-10, mode=mode, trace_len=10)
+        torch.cuda.synchronize()
+        out[on] = (x.cpu().numpy(), res)
+        op.close()
+    assert np.array_equal(out[True][0], out[False][0])
+    assert out[True][1]["iterations"] == out[False][1]["iterations"]
+    assert np.array_equal(out[True][1]["trace"], out[False][1]["trace"])
+    ref = oracle.cg(rp, c, v, b, rtol=1e-10)
+    assert np.linalg.norm(out[True][0] - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+
+
+def test_vector_cache_skipped_when_rows_do_not_fit(ctx):
+    """2^21 rows of one nonzero each: a block's rows (about 6.9k, 166 KB of
+    cache) no longer let two blocks share an SM, so the solve keeps its
+    vectors in global memory and still converges (A = 2 I: one iteration)."""
+    n = 1 << 21
+    rp = np.arange(n + 1, dtype=np.int32)
+    c = np.arange(n, dtype=np.int32)
+    v = np.full(n, 2.0)
+    b = inputs.cg_rhs(n, 21)
+    op = _op(ctx, rp, c, v)
+    assert not op.vector_cache_active
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = op.solve(_dev(b), x, rtol=1e-12)
+    assert res["true_rel_residual"] <= 1e-12
+    assert np.max(np.abs(x.cpu().numpy() - b / 2.0)) <= 1e-15
+    op.close()
