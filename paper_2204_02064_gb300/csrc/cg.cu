@@ -406,10 +406,14 @@ perks_status configure(perks_op *op) {
     op->smem_vc = kCgRowvecSmem + (((size_t)op->max_rows2 * kCgVcacheBytesPerRow + 15) & ~size_t(15));
     op->vcache_ok = false;
     // (the attribute is per function, shared by every operator: set to the
-    // device limit; each launch passes its own size)
-    if (op->smem_vc <= (size_t)ctx->smem_optin &&
+    // device limit less the kernel's static shared memory; each launch passes
+    // its own size)
+    cudaFuncAttributes fa0;
+    PERKS_CUDA(ctx, cudaFuncGetAttributes(&fa0, (const void *)perks_cg_kernel<0>));
+    const int dyn_max = ctx->smem_optin - (int)fa0.sharedSizeBytes;
+    if (op->smem_vc <= (size_t)dyn_max &&
         cudaFuncSetAttribute((const void *)perks_cg_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             ctx->smem_optin) == cudaSuccess) {
+                             dyn_max) == cudaSuccess) {
         int per_vc = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_vc, (const void *)perks_cg_kernel<0>, kCgThreads,
                                                           op->smem_vc) == cudaSuccess)
@@ -508,7 +512,8 @@ perks_status read_result(perks_op *op, cudaStream_t s, perks_cg_stats *stats) {
         // once, and the vector updates: q, x, r, p read/written per iteration.
         // With the vector cache, x (d), r and q stay on chip: p's gather,
         // its read in the update and its read and write in the direction remain.
-        const bool vc = op->spmv_kind == PERKS_SPMV_ROWVEC && op->vcache_ok && op->vcache_on;
+        const bool vc = op->spmv_kind == PERKS_SPMV_ROWVEC && op->vcache_ok && op->vcache_on &&
+                        op->last_mode != PERKS_CG_FP64_MULTI;
         stats->bytes_per_iteration = op->nnz * (vbytes + 4.0) + 4.0 * (op->n + 1.0) +
                                      vbytes * op->n * (vc ? 1.0 + 1.0 + 2.0
                                                           : 1.0 + 1.0 + 2.0 + 2.0 + 2.0 + 2.0);
