@@ -336,15 +336,18 @@ enum { PERKS_SPMV_ROWVEC = 0, PERKS_SPMV_MERGE = 1, PERKS_SPMV_SEG = 2 };
 perks_status perks_op_set_spmv(perks_op *op, int32_t kind);
 
 /* Vector cache of the persistent CG with the ROWVEC SpMV (the caching of the
- * residual vector of Sec. 4.3.2, extended to every vector only one block
- * touches): each block keeps its rows of x, r and q (fp64 solve) or of the
- * inner r, d and q (FP32_IR) in shared memory for the whole solve; p, which
- * every block gathers, stays in global memory.  on = 1 (default) uses it
- * when the largest block's rows fit (24 bytes per row) with all blocks
- * co-resident; 0 keeps every vector in global memory.  Results are
- * identical either way.  Errors: INVALID_ARG. */
-perks_status perks_op_set_vector_cache(perks_op *op, int32_t on);
-/* 1 if the next persistent solve of `op` runs with the vector cache. */
+ * residual vector of Sec. 4.3.2): each block keeps its rows of vectors only
+ * it touches in shared memory for the whole solve -- level 1: r (the inner
+ * r for FP32_IR); level 2: x, r and q (inner r, d and q); p, which every
+ * block gathers, stays in global memory.  Level 0 (default) keeps every
+ * vector in global memory.  A level takes effect when the largest block's
+ * rows fit at 24 bytes per row with all blocks co-resident.  Results are
+ * identical at every level.  On GB300 the cache is slower (n = 2^20 to 1e-8:
+ * 9.7 ms without, 12.6 ms at level 2): the shared memory it takes comes out
+ * of the unified L1, which holds the SpMV's gathers in flight.  Errors:
+ * INVALID_ARG. */
+perks_status perks_op_set_vector_cache(perks_op *op, int32_t level);
+/* The level the next persistent solve of `op` runs with (0: none). */
 int32_t perks_op_vector_cache_active(const perks_op *op);
 
 /* y = A x for device vectors of n doubles (one launch). */

@@ -458,14 +458,15 @@ class CsrOperator:
         segment at a time; its layout is built on first selection)."""
         self.ctx.check(self._lib.perks_op_set_spmv(self.handle, int(kind)))
 
-    def set_vector_cache(self, on: bool):
-        """Keep each block's rows of x, r, q (fp32 inner: r, d, q) in shared
-        memory during a persistent solve with SPMV_ROWVEC (default on)."""
-        self.ctx.check(self._lib.perks_op_set_vector_cache(self.handle, 1 if on else 0))
+    def set_vector_cache(self, level: int):
+        """Vectors each block keeps in shared memory during a persistent
+        solve with SPMV_ROWVEC: 0 none (default), 1 r, 2 x, r, q (fp32
+        inner: r; r, d, q)."""
+        self.ctx.check(self._lib.perks_op_set_vector_cache(self.handle, int(level)))
 
     @property
-    def vector_cache_active(self) -> bool:
-        return bool(self._lib.perks_op_vector_cache_active(self.handle))
+    def vector_cache_active(self) -> int:
+        return int(self._lib.perks_op_vector_cache_active(self.handle))
 
     def spmv(self, x, y, stream=None):
         xp, xd, _ = _buffer(x)

@@ -292,7 +292,7 @@ struct perks_op {
     int max_rows2 = 0;                                  // rows of the largest row-vector block
     size_t smem_vc = 0;                                 // row-vector kernel's shared memory with the vector cache
     bool vcache_ok = false;                             // the cache fits with G2 blocks co-resident
-    bool vcache_on = true;                              // perks_op_set_vector_cache
+    int vcache_level = 0;                               // perks_op_set_vector_cache
     int2 *part_tiles2 = nullptr;
     // column-segmented SpMV: G blocks (part_row), layout built on first use
     bool seg_built = false;
@@ -365,7 +365,7 @@ CgArgs make_args(perks_op *op, double rtol, int max_iter, int mode, double inner
     a.mode = mode;
     a.allow_cache = 1;
     a.spmv_kind = op->spmv_kind;
-    a.vcache = rv && op->vcache_ok && op->vcache_on && mode != CGK_SPMV;
+    a.vcache = rv && op->vcache_ok && mode != CGK_SPMV ? op->vcache_level : 0;
     a.vcache_rows = op->max_rows2;
     a.seg.nseg = op->nseg;
     a.seg.val = op->sval;
@@ -429,6 +429,13 @@ perks_status configure(perks_op *op) {
     return PERKS_OK;
 }
 
+// Shared memory of the row-vector kernel at vector-cache level `level`.
+size_t rowvec_smem(const perks_op *op, int level) {
+    if (level <= 0) return kCgRowvecSmem;
+    const size_t per_row = level == 1 ? sizeof(double) : kCgVcacheBytesPerRow;
+    return kCgRowvecSmem + (((size_t)op->max_rows2 * per_row + 15) & ~size_t(15));
+}
+
 perks_status launch_persistent(perks_op *op, const CgArgs &a, cudaStream_t s) {
     perks_context *ctx = op->ctx;
     PERKS_CUDA(ctx, cudaMemsetAsync(op->bar, 0, sizeof(unsigned long long), s));
@@ -436,8 +443,7 @@ perks_status launch_persistent(perks_op *op, const CgArgs &a, cudaStream_t s) {
     void *args[] = {(void *)&a};
     if (op->spmv_kind == PERKS_SPMV_ROWVEC)
         PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<0>, dim3(op->G2),
-                                                    dim3(kCgThreads), args,
-                                                    a.vcache ? op->smem_vc : kCgRowvecSmem, s));
+                                                    dim3(kCgThreads), args, rowvec_smem(op, a.vcache), s));
     else if (op->spmv_kind == PERKS_SPMV_SEG)
         PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)perks_cg_kernel<2>, dim3(op->G),
                                                     dim3(kCgThreads), args, seg_smem_bytes(), s));
@@ -512,11 +518,12 @@ perks_status read_result(perks_op *op, cudaStream_t s, perks_cg_stats *stats) {
         // once, and the vector updates: q, x, r, p read/written per iteration.
         // With the vector cache, x (d), r and q stay on chip: p's gather,
         // its read in the update and its read and write in the direction remain.
-        const bool vc = op->spmv_kind == PERKS_SPMV_ROWVEC && op->vcache_ok && op->vcache_on &&
-                        op->last_mode != PERKS_CG_FP64_MULTI;
-        stats->bytes_per_iteration = op->nnz * (vbytes + 4.0) + 4.0 * (op->n + 1.0) +
-                                     vbytes * op->n * (vc ? 1.0 + 1.0 + 2.0
-                                                          : 1.0 + 1.0 + 2.0 + 2.0 + 2.0 + 2.0);
+        const int lvl = op->spmv_kind == PERKS_SPMV_ROWVEC && op->vcache_ok &&
+                                op->last_mode != PERKS_CG_FP64_MULTI ? op->vcache_level : 0;
+        // per element: p gathered 1, q written 1 and read 1, x (d) 2, r 2 in
+        // the update, p 2 and r 1 in the direction (less what stays on chip)
+        const double vec_terms = lvl == 2 ? 4.0 : lvl == 1 ? 7.0 : 10.0;
+        stats->bytes_per_iteration = op->nnz * (vbytes + 4.0) + 4.0 * (op->n + 1.0) + vbytes * op->n * vec_terms;
         if (stats->trace && stats->trace_len > 0) {
             const int k = std::min(std::min(stats->trace_len, op->trace_cap), r.iterations);
             if (k > 0)
@@ -812,15 +819,15 @@ extern "C" perks_status perks_cg_last_result(perks_op *op, perks_stream stream, 
     return read_result(op, (cudaStream_t)stream, stats ? stats : &local);
 }
 
-extern "C" perks_status perks_op_set_vector_cache(perks_op *op, int32_t on) {
+extern "C" perks_status perks_op_set_vector_cache(perks_op *op, int32_t level) {
     if (!op) return PERKS_ERR_INVALID_ARG;
-    if (on != 0 && on != 1) return fail(op->ctx, PERKS_ERR_INVALID_ARG, "op_set_vector_cache: 0 or 1");
-    op->vcache_on = on != 0;
+    if (level < 0 || level > 2) return fail(op->ctx, PERKS_ERR_INVALID_ARG, "op_set_vector_cache: level 0, 1 or 2");
+    op->vcache_level = level;
     return PERKS_OK;
 }
 
 extern "C" int32_t perks_op_vector_cache_active(const perks_op *op) {
-    return op && op->vcache_ok && op->vcache_on && op->spmv_kind == PERKS_SPMV_ROWVEC ? 1 : 0;
+    return op && op->vcache_ok && op->spmv_kind == PERKS_SPMV_ROWVEC ? op->vcache_level : 0;
 }
 
 extern "C" perks_status perks_op_set_spmv(perks_op *op, int32_t kind) {

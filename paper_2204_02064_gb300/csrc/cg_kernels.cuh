@@ -74,7 +74,7 @@ struct CgArgs {
     int mode;
     int allow_cache;
     int spmv_kind;           // 0: row-vector SpMV (default), 1: thread-level merge walk, 2: column-segmented
-    int vcache;              // row-vector kind: the block's rows of x, r, q (fp64) or r32, d32, q32 in shared memory
+    int vcache;              // row-vector kind, vectors kept in shared memory: 0 none, 1 r (r32), 2 x, r, q (r32, d32, q32)
     int vcache_rows;         // rows of the largest block (capacity of each cached vector)
     const double *spmv_in;
     double *spmv_out;
@@ -512,21 +512,23 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
     double *x = a.x, *r = a.r, *p = a.p, *q = a.q;
 
     // Vector cache (row-vector kind; the paper's caching of r, Sec. 4.3.2):
-    // the vectors only this block touches -- x, r, q in fp64, r32, d32, q32
-    // in the fp32 inner solves -- stay in shared memory for the whole solve;
-    // p (p32), gathered by every block, stays in global memory.  x goes back
-    // to global memory before each true-residual SpMV (which gathers it) and
-    // at the end.
-    const bool vc64 = KIND == 0 && a.vcache && a.mode == CGK_FP64;
-    const bool vc32 = KIND == 0 && a.vcache && a.mode == CGK_FP32_IR;
+    // vectors only this block touches stay in shared memory for the whole
+    // solve -- level 1: r (r32 in the fp32 inner solves); level 2: x, r, q
+    // (r32, d32, q32).  p (p32), gathered by every block, stays in global
+    // memory.  A cached x goes back to global memory before each
+    // true-residual SpMV (which gathers it) and at the end.
+    const bool vr64 = KIND == 0 && a.vcache >= 1 && a.mode == CGK_FP64;
+    const bool vc64 = KIND == 0 && a.vcache >= 2 && a.mode == CGK_FP64;
+    const bool vr32 = KIND == 0 && a.vcache >= 1 && a.mode == CGK_FP32_IR;
+    const bool vc32 = KIND == 0 && a.vcache >= 2 && a.mode == CGK_FP32_IR;
     const int cap = a.vcache_rows;
-    double *xs = reinterpret_cast<double *>(smem_raw + kCgRowvecSmem);
-    double *rs = xs + cap, *qs = rs + cap;
+    double *rs = reinterpret_cast<double *>(smem_raw + kCgRowvecSmem);
+    double *xs = rs + cap, *qs = xs + cap;
     float *r32s = reinterpret_cast<float *>(smem_raw + kCgRowvecSmem);
     float *d32s = r32s + cap, *q32s = d32s + cap;
     const int r0 = sl.r0;
     auto X = [&](int i) -> double & { return vc64 ? xs[i - r0] : x[i]; };
-    auto R = [&](int i) -> double & { return vc64 ? rs[i - r0] : r[i]; };
+    auto R = [&](int i) -> double & { return vr64 ? rs[i - r0] : r[i]; };
     auto Q = [&](int i) -> double & { return vc64 ? qs[i - r0] : q[i]; };
     auto put_x = [&]() {  // cached x -> global x (own rows)
         if (vc64)
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(kCgThreads, KIND == 0 ? 2 : 1) perks_cg_kernel
         put_x();
     } else {  // CGK_FP32_IR
         float *r32 = a.r32, *p32 = a.p32, *q32 = a.q32, *d32 = a.d32;
-        auto R32 = [&](int i) -> float & { return vc32 ? r32s[i - r0] : r32[i]; };
+        auto R32 = [&](int i) -> float & { return vr32 ? r32s[i - r0] : r32[i]; };
         auto D32 = [&](int i) -> float & { return vc32 ? d32s[i - r0] : d32[i]; };
         auto Q32 = [&](int i) -> float & { return vc32 ? q32s[i - r0] : q32[i]; };
         for (;;) {

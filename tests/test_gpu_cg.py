@@ -263,26 +263,47 @@ def test_cg_nan_rhs_reports_breakdown(ctx):
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "fp32_ir"])
-def test_vector_cache_on_off_identical(ctx, oracle, system_4k, mode):
-    """The vector cache (each block's rows of x, r, q -- or the inner r, d, q
-    -- in shared memory) changes where values live, not the arithmetic: the
-    solutions and iteration counts are identical with it on and off."""
+def test_vector_cache_levels_identical(ctx, oracle, system_4k, mode):
+    """The vector cache (each block's rows of r, or of x, r, q -- the inner
+    r, or r, d, q -- in shared memory) changes where values live, not the
+    arithmetic: solutions, iteration counts and traces are identical at
+    every level."""
     rp, c, v, b = system_4k
     out = {}
-    for on in (True, False):
+    for level in (0, 1, 2):
         op = _op(ctx, rp, c, v)
-        op.set_vector_cache(on)
-        assert op.vector_cache_active == on
+        op.set_vector_cache(level)
+        assert op.vector_cache_active == level
         x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
         res = op.solve(_dev(b), x, rtol=1e-10, mode=mode, trace_len=10)
         torch.cuda.synchronize()
-        out[on] = (x.cpu().numpy(), res)
+        out[level] = (x.cpu().numpy(), res)
         op.close()
-    assert np.array_equal(out[True][0], out[False][0])
-    assert out[True][1]["iterations"] == out[False][1]["iterations"]
-    assert np.array_equal(out[True][1]["trace"], out[False][1]["trace"])
+    for level in (1, 2):
+        assert np.array_equal(out[level][0], out[0][0])
+        assert out[level][1]["iterations"] == out[0][1]["iterations"]
+        assert np.array_equal(out[level][1]["trace"], out[0][1]["trace"])
     ref = oracle.cg(rp, c, v, b, rtol=1e-10)
-    assert np.linalg.norm(out[True][0] - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+    assert np.linalg.norm(out[2][0] - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
+
+
+def test_vector_cache_full_size(ctx, system_full):
+    """n = 2^20 with every vector the blocks own in shared memory: fp64 and
+    fp32-IR reach 1e-10 with the same iteration counts as without."""
+    from paper_2204_02064_gb300 import api
+    rp, c, v, b = system_full
+    for mode in (api.CG_FP64, api.CG_FP32_IR):
+        its = {}
+        for level in (0, 2):
+            op = _op(ctx, rp, c, v)
+            op.set_vector_cache(level)
+            assert op.vector_cache_active == level
+            x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+            res = op.solve(_dev(b), x, rtol=1e-10, mode=mode)
+            assert res["true_rel_residual"] <= 1e-10
+            its[level] = res["iterations"]
+            op.close()
+        assert its[0] == its[2]
 
 
 def test_vector_cache_skipped_when_rows_do_not_fit(ctx):
@@ -295,7 +316,8 @@ def test_vector_cache_skipped_when_rows_do_not_fit(ctx):
     v = np.full(n, 2.0)
     b = inputs.cg_rhs(n, 21)
     op = _op(ctx, rp, c, v)
-    assert not op.vector_cache_active
+    op.set_vector_cache(2)
+    assert op.vector_cache_active == 0
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     res = op.solve(_dev(b), x, rtol=1e-12)
     assert res["true_rel_residual"] <= 1e-12
