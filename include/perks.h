@@ -447,6 +447,13 @@ perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
  * with BARRIER_TIMEOUT (reported when stats are requested).  Errors:
  * INVALID_ARG. */
 perks_status perks_poisson_set_group(perks_poisson *p, int32_t blocks);
+/* Rows of a grid column each thread takes per pass of the matvec: 4
+ * (default; each column value and face loaded once for 4 cells, 128
+ * registers, one 512-thread block per SM) or 1 (64 registers, two 512-thread
+ * blocks per SM: twice the warps to hide load latency, more load
+ * instructions per cell).  Overrides the block shape of
+ * perks_poisson_set_block_threads while set to 1.  Errors: INVALID_ARG. */
+perks_status perks_poisson_set_rows_per_pass(perks_poisson *p, int32_t rows);
 
 
 /* ------------------------------------------------------------------------ */

@@ -138,6 +138,7 @@ def _declare(lib):
         "perks_poisson_set_block_threads": ([P, i32], i32),
         "perks_poisson_scale_guess": ([P, P, P, P], i32),
         "perks_poisson_set_group": ([P, i32], i32),
+        "perks_poisson_set_rows_per_pass": ([P, i32], i32),
         "perks_warmnet_create": ([P, P, i32, ctypes.c_uint64, ctypes.POINTER(P)], i32),
         "perks_warmnet_destroy": ([P], i32),
         "perks_warmnet_num_params": ([P], i32),
@@ -618,6 +619,11 @@ class Poisson:
     def set_block_threads(self, threads: int):
         """512 (one block per SM, default) or 256 threads per problem's block."""
         self.ctx.check(self._lib.perks_poisson_set_block_threads(self.handle, int(threads)))
+
+    def set_rows_per_pass(self, rows: int):
+        """4 (default: 128 registers, one 512-thread block per SM) or 1 (64
+        registers, two blocks per SM)."""
+        self.ctx.check(self._lib.perks_poisson_set_rows_per_pass(self.handle, int(rows)))
 
     def set_group(self, blocks: int):
         """Blocks per problem: 0 (automatic, default), 1, 2, 4 or 8 (rows split over the group)."""

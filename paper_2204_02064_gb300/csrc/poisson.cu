@@ -431,6 +431,7 @@ struct perks_poisson {
     int *queue = nullptr, *iters = nullptr, *status = nullptr;
     double *true_rel = nullptr;
     int block_threads = 512;  // 512 (one block per SM; measured faster) or 256 (two per SM)
+    int rows_per_pass = kRows;  // kRows (128 registers, 16 warps per SM) or 1 (64 registers, 32 warps)
     int group = 0;            // blocks per problem (0: automatic)
     unsigned long long *gbar = nullptr;
     int *gprob = nullptr;
@@ -567,7 +568,10 @@ extern "C" perks_status perks_poisson_solve(perks_poisson *P, const double *b, d
     const int C = effective_group(P);
     const bool grouped = C > 1;
     const void *kern;
-    if (P->block_threads == 512)
+    if (P->rows_per_pass == 1)  // two 512-thread blocks per SM, one row per pass
+        kern = grouped ? (const void *)perks_poisson_cg_kernel<512, 2, 1, 1, true>
+                       : (const void *)perks_poisson_cg_kernel<512, 2, 1, 1, false>;
+    else if (P->block_threads == 512)
         kern = grouped ? (const void *)perks_poisson_cg_kernel<512, 1, kRows, kLin, true>
                        : (const void *)perks_poisson_cg_kernel<512, 1, kRows, kLin, false>;
     else
@@ -639,6 +643,14 @@ extern "C" perks_status perks_poisson_set_group(perks_poisson *P, int32_t blocks
     if (blocks != 0 && blocks != 1 && blocks != 2 && blocks != 4 && blocks != 8)
         return fail(P->ctx, PERKS_ERR_INVALID_ARG, "poisson_set_group: 0 (automatic), 1, 2, 4 or 8 blocks");
     P->group = blocks;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_poisson_set_rows_per_pass(perks_poisson *P, int32_t rows) {
+    if (!P) return PERKS_ERR_INVALID_ARG;
+    if (rows != 1 && rows != kRows)
+        return fail(P->ctx, PERKS_ERR_INVALID_ARG, "poisson_set_rows_per_pass: 1 or %d", kRows);
+    P->rows_per_pass = rows;
     return PERKS_OK;
 }
 

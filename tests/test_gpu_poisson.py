@@ -179,3 +179,28 @@ def test_automatic_block_groups(ctx):
         assert res["grid_blocks"] == nprob * per
         assert res["max_true_rel_residual"] <= 1e-8
         P.close()
+
+
+@pytest.mark.parametrize("group", [1, 4])
+def test_one_row_per_pass_matches_oracle(ctx, oracle, group):
+    """The 64-register kernel (one row per pass, two blocks per SM), with one
+    block or a group of four per problem, agrees with the oracle's CG."""
+    from paper_2204_02064_gb300 import api
+    nprob, ny, nx = 9, 37, 45
+    k = _k(nprob, ny, nx, 17)
+    f = 2.0 * inputs.uniform(18, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
+    P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    P.set_rows_per_pass(1)
+    P.set_group(group)
+    x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
+    res = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
+    xs = x.cpu().numpy()
+    assert res["max_true_rel_residual"] <= 1e-8
+    for i in range(0, nprob, 4):
+        rp, c, val = oracle.poisson_csr(k[i])
+        ref = oracle.cg(rp, c, val, f[i].ravel(), rtol=1e-8, max_iter=20000)
+        assert abs(int(res["iterations"][i]) - ref["iters"]) <= 2
+        assert np.linalg.norm(xs[i].ravel() - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    with pytest.raises(api.PerksError):
+        P.set_rows_per_pass(3)
+    P.close()
