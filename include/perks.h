@@ -434,9 +434,10 @@ perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, d
  * where the larger block is faster (256 problems of 512^2: 23.6 s vs
  * 31.8 s to 1e-8).  Errors: INVALID_ARG. */
 perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
-/* Blocks per problem: 1, 2, 4 or 8, or 0 (the default: 4 for problems of
- * 65536 cells and more, 1 below; 256 problems of 512^2 to 1e-8 take 20.2 s
- * with C = 1, 16.4 s with 2 and 15.9 s with 4).  With C > 1 each problem's
+/* Blocks per problem: 1, 2, 4 or 8, or 0 (the default: for problems of
+ * 65536 cells and more 8 with one row per pass, 4 with four, and 1 below;
+ * 256 problems of 512^2 to 1e-8 at four rows per pass take 20.2 s with C =
+ * 1, 16.4 s with 2 and 15.9 s with 4).  With C > 1 each problem's
  * rows are split over a group of C blocks that meet at a bounded barrier of
  * their own after every p update and in every dot product (the group's block
  * sums are added in rank order, so all its blocks take the same decisions);
@@ -447,12 +448,14 @@ perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
  * with BARRIER_TIMEOUT (reported when stats are requested).  Errors:
  * INVALID_ARG. */
 perks_status perks_poisson_set_group(perks_poisson *p, int32_t blocks);
-/* Rows of a grid column each thread takes per pass of the matvec: 4
- * (default; each column value and face loaded once for 4 cells, 128
- * registers, one 512-thread block per SM) or 1 (64 registers, two 512-thread
- * blocks per SM: twice the warps to hide load latency, more load
- * instructions per cell).  Overrides the block shape of
- * perks_poisson_set_block_threads while set to 1.  Errors: INVALID_ARG. */
+/* Rows of a grid column each thread takes per pass of the matvec: 1
+ * (default: 64 registers, two 512-thread blocks per SM, twice the warps to
+ * hide load latency) or 4 (each column value and face loaded once for 4
+ * cells, 128 registers, one block per SM, or two of 256 threads, as
+ * perks_poisson_set_block_threads says).  256 problems of 512^2 to 1e-8,
+ * automatic groups: 13.4 s with 1, 15.9 s with 4.  The block shape of
+ * perks_poisson_set_block_threads applies with 4 only.  Errors:
+ * INVALID_ARG. */
 perks_status perks_poisson_set_rows_per_pass(perks_poisson *p, int32_t rows);
 
 

@@ -431,7 +431,7 @@ struct perks_poisson {
     int *queue = nullptr, *iters = nullptr, *status = nullptr;
     double *true_rel = nullptr;
     int block_threads = 512;  // 512 (one block per SM; measured faster) or 256 (two per SM)
-    int rows_per_pass = kRows;  // kRows (128 registers, 16 warps per SM) or 1 (64 registers, 32 warps)
+    int rows_per_pass = 1;    // 1 (64 registers, 32 warps per SM; measured faster) or kRows (128, 16 warps)
     int group = 0;            // blocks per problem (0: automatic)
     unsigned long long *gbar = nullptr;
     int *gprob = nullptr;
@@ -447,13 +447,16 @@ void free_poisson(perks_poisson *P) {
     for (void *v : ptrs) if (v) cudaFree(v);
 }
 
-// Blocks per problem: as set, or automatically 4 for problems of 64K cells
-// and more (a batch of 256 problems of 512^2: 20.2 s with one block per
-// problem, 16.4 s with 2, 15.9 s with 4 or 8) and 1 for smaller ones (whose
-// iterations are too short to pay for the group barriers).
+// Blocks per problem: as set, or automatically, for problems of 64K cells
+// and more, 8 blocks (two per SM, one row per pass) or 4 (one per SM, 4
+// rows per pass), and 1 for smaller problems (whose iterations are too short
+// to pay for the group barriers).  A batch of 256 problems of 512^2 to 1e-8:
+// 4 rows per pass 20.2 s with one block per problem, 16.4 s with 2, 15.9 s
+// with 4 or 8; one row per pass 16.3 s with 2, 13.5 s with 4, 13.4 s with 8.
 int effective_group(const perks_poisson *P) {
     if (P->group > 0) return P->group;
-    return P->n >= 65536 ? 4 : 1;
+    if (P->n < 65536) return 1;
+    return P->rows_per_pass == 1 ? 8 : 4;
 }
 
 PoissonArgs poisson_args(perks_poisson *P) {

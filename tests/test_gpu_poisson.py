@@ -76,6 +76,7 @@ def test_block_shapes_agree(ctx):
     res = []
     for threads in (256, 512):
         P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+        P.set_rows_per_pass(4)  # the block shape applies to the 4-row kernel
         P.set_block_threads(threads)
         x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
         r = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
@@ -116,9 +117,10 @@ def test_scale_guess_matches_oracle(ctx, oracle):
     P.close()
 
 
+@pytest.mark.parametrize("rows", [1, 4])
 @pytest.mark.parametrize("group", [2, 4, 8])
 @pytest.mark.parametrize("nprob,ny,nx", [(5, 24, 31), (40, 37, 16)])
-def test_block_groups_match_oracle(ctx, oracle, group, nprob, ny, nx):
+def test_block_groups_match_oracle(ctx, oracle, group, nprob, ny, nx, rows):
     """Rows of each problem split over a group of blocks (37 rows over 8
     blocks leaves some blocks one row block or none): every problem reaches
     the tolerance and agrees with the oracle's CG."""
@@ -126,6 +128,7 @@ def test_block_groups_match_oracle(ctx, oracle, group, nprob, ny, nx):
     k = _k(nprob, ny, nx, 11)
     f = 2.0 * inputs.uniform(12, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0
     P = api.Poisson(ctx, torch.from_numpy(k).cuda())
+    P.set_rows_per_pass(rows)
     P.set_group(group)
     x = torch.zeros(nprob, ny, nx, dtype=torch.float64, device="cuda")
     res = P.solve(torch.from_numpy(f).cuda(), x, rtol=1e-8)
@@ -166,10 +169,10 @@ def test_block_group_barrier_timeout_reported(ctx):
 
 
 def test_automatic_block_groups(ctx):
-    """By default problems of 64K cells and more get groups of 4 blocks,
-    smaller ones one block each."""
+    """By default problems of 64K cells and more get groups of 8 blocks (two
+    per SM, one row per pass), smaller ones one block each."""
     from paper_2204_02064_gb300 import api
-    for ny, nx, per in ((256, 256, 4), (64, 64, 1)):
+    for ny, nx, per in ((256, 256, 8), (64, 64, 1)):
         nprob = 3
         k = _k(nprob, ny, nx, 15)
         f = torch.from_numpy(2.0 * inputs.uniform(16, nprob * ny * nx).reshape(nprob, ny, nx) - 1.0).cuda()
