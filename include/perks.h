@@ -428,11 +428,12 @@ perks_status perks_poisson_scale_guess(perks_poisson *p, const double *b, double
  * then returns the first failing problem's status. */
 perks_status perks_poisson_solve(perks_poisson *p, const double *b, double *x, double rtol,
                                  int32_t max_iter, perks_stream stream, perks_poisson_stats *stats);
-/* Block shape of the solve: 512 threads (one block per SM, default) or 256
- * (two per SM: twice as many problems at a time, half the loads in flight
- * per problem).  A batch finishes with its slowest problem running alone,
- * where the larger block is faster (256 problems of 512^2: 23.6 s vs
- * 31.8 s to 1e-8).  Errors: INVALID_ARG. */
+/* Block shape of the 4-rows-per-pass kernel (perks_poisson_set_rows_per_pass):
+ * 512 threads (one block per SM, default) or 256 (two per SM: twice as many
+ * blocks, half the loads in flight per block).  With one block per problem
+ * a batch finishes with its slowest problem running alone, where the larger
+ * block is faster (256 problems of 512^2 to 1e-8, before the diagonal was
+ * precomputed: 23.6 s vs 31.8 s).  Errors: INVALID_ARG. */
 perks_status perks_poisson_set_block_threads(perks_poisson *p, int32_t threads);
 /* Blocks per problem: 1, 2, 4 or 8, or 0 (the default: for problems of
  * 65536 cells and more 8 with one row per pass, 4 with four, and 1 below;
