@@ -237,17 +237,24 @@ perks_status perks_stencil_get_field(perks_stencil *st, void *dst, int dst_on_de
  * record) is one static device array compiled into the library, about 12 MiB,
  * held on every GPU that loads the library until the process exits.  Limits:
  * nx*ny*nz <= 2^20 cells and the plan's x-edge buffers <= 4 MiB; larger
- * problems return PERKS_ERR_INVALID_ARG before any GPU work.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call outside any stream capture.  Every call reuses the
- * same array and clears its counter and error record, so calls whose kernels
- * overlap on the GPU (other streams, other host threads) race.
+ * problems (each extent is checked before their product is formed) return
+ * PERKS_ERR_INVALID_ARG before any GPU work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process; make that first call outside any stream capture,
+ * and do not use this entry point on a device after cudaDeviceReset (the
+ * kept address would be stale).  Every call reuses the same array and clears
+ * its counter and error record, so calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race.
+ *
+ * Besides device memory, the call makes no heap allocation on the host
+ * either, except that the library's table of compiled kernels is built on
+ * the first call in the process that plans any stencil run (once).  No
+ * message is formatted or recorded (there is no context).
  *
  * sync == 0: asynchronous, device-side errors are not reported; sync != 0:
  * synchronizes `stream` and returns PERKS_ERR_BARRIER_TIMEOUT if a grid
  * barrier wait ran past 2 s.  Other errors: INVALID_ARG, UNSUPPORTED (shape
- * or dtype without a persistent kernel), LAUNCH_TOO_LARGE, CUDA.  No message
- * is recorded (there is no context). */
+ * or dtype without a persistent kernel), LAUNCH_TOO_LARGE, CUDA. */
 perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc, const void *in, void *out,
                                        int64_t steps, perks_stream stream, int32_t sync);
 

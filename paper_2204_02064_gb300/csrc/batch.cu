@@ -122,8 +122,6 @@ struct BatchKernel {
     int dtype;
     int v, d;
     BatchFn fn;
-    bool configured = false;
-    int smem_budget = 0;
 };
 
 std::vector<BatchKernel> &batch_kernels() {
@@ -230,6 +228,11 @@ struct PlanOut {
 
 // Plans tiles, assignment and cache split for a granularity and width cap.
 perks_status plan_batch(perks_batch *b, BatchKernel &k, double granularity, int width_cap, PlanOut &o) {
+    int smem_budget = 0;  // dynamic shared memory per block on this device (limit raised once per device)
+    {
+        const perks_status rc = smem_optin(b->ctx, (const void *)k.fn, &smem_budget);
+        if (rc) return rc;
+    }
     perks_context *ctx = b->ctx;
     const int G = ctx->sm_count;  // one block per SM
     const int V = k.v;
@@ -280,7 +283,7 @@ perks_status plan_batch(perks_batch *b, BatchKernel &k, double granularity, int 
     o.ring_elems = (long long)S * (txmax_all + 2 * HX);
     o.ring_elems = (o.ring_elems + 15) & ~15ll;
     const long long ring_bytes = o.ring_elems * es;
-    if (ring_bytes > k.smem_budget) return fail(ctx, PERKS_ERR_UNSUPPORTED, "batch: ring exceeds shared memory");
+    if (ring_bytes > smem_budget) return fail(ctx, PERKS_ERR_UNSUPPORTED, "batch: ring exceeds shared memory");
 
     // per-tile geometry and model cost (Sec. 5.2: bytes / per-SM bandwidth,
     // plus a pipeline fill per tile visit)
@@ -318,7 +321,7 @@ perks_status plan_batch(perks_batch *b, BatchKernel &k, double granularity, int 
     double makespan = 0.0;
     for (int bb = 0; bb < G; ++bb) {
         o.block_first[bb] = (int)o.tile_list.size();
-        long long free_elems = (k.smem_budget - ring_bytes) / es;
+        long long free_elems = (smem_budget - ring_bytes) / es;
         long long off = 0;
         double t_block = 0.0;
         for (int q : per_block[bb]) {
@@ -399,14 +402,6 @@ perks_status upload_plan(perks_batch *b, const PlanOut &o) {
 perks_status ensure_plan(perks_batch *b) {
     BatchKernel *k = batch_kernel(b);
     if (!k) return fail(b->ctx, PERKS_ERR_UNSUPPORTED, "batch: no kernel for this dtype");
-    if (!k->configured) {
-        cudaFuncAttributes fa;
-        PERKS_CUDA(b->ctx, cudaFuncGetAttributes(&fa, (const void *)k->fn));
-        k->smem_budget = b->ctx->smem_optin - (int)fa.sharedSizeBytes;
-        PERKS_CUDA(b->ctx, cudaFuncSetAttribute((const void *)k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                k->smem_budget));
-        k->configured = true;
-    }
     if (b->blocks > 0) return PERKS_OK;
     PlanOut o;
     perks_status rc = plan_batch(b, *k, b->granularity, b->width_cap, o);

@@ -1,9 +1,54 @@
 // Context entry points of the C ABI: device queries, error messages and the
 // barrier time limit shared by every persistent launch.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
 using namespace perks;
+
+namespace perks {
+
+struct OptinRecord {
+    const void *fn;
+    int static_smem;
+    unsigned long long devices;  // bit d: the limit is raised on device d
+};
+static constexpr int kOptinSlots = 2048;
+static OptinRecord g_optin[kOptinSlots];
+static int g_optin_used = 0;
+static std::mutex g_optin_mutex;
+
+perks_status smem_optin(perks_context *ctx, const void *fn, int *budget) {
+    std::lock_guard<std::mutex> lock(g_optin_mutex);
+    OptinRecord *rec = nullptr;
+    for (int i = 0; i < g_optin_used; ++i)
+        if (g_optin[i].fn == fn) { rec = &g_optin[i]; break; }
+    int static_smem;
+    if (rec) {
+        static_smem = rec->static_smem;
+    } else {
+        cudaFuncAttributes fa;
+        PERKS_CUDA(ctx, cudaFuncGetAttributes(&fa, fn));
+        static_smem = (int)fa.sharedSizeBytes;
+        if (g_optin_used < kOptinSlots) {
+            rec = &g_optin[g_optin_used++];
+            rec->fn = fn;
+            rec->static_smem = static_smem;
+            rec->devices = 0;
+        }
+    }
+    const int b = ctx->smem_optin - static_smem;
+    const bool known = rec && ctx->device < 64 && (rec->devices >> ctx->device & 1ull);
+    if (!known) {
+        PERKS_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        if (rec && ctx->device < 64) rec->devices |= 1ull << ctx->device;
+    }
+    *budget = b;
+    return PERKS_OK;
+}
+
+}  // namespace perks
 
 namespace {
 

@@ -18,18 +18,20 @@ struct perks_context {
     long long l2_bytes = 0;
     int cooperative = 0;
     long long timeout_ns = 2000000000LL;
+    bool quiet = false;        // record no message (a stack context of an allocation-free call)
     std::string last_error = "no error";
 };
 
 namespace perks {
 
 inline perks_status fail(perks_context *ctx, perks_status st, const char *fmt, ...) {
+    if (!ctx || ctx->quiet) return st;
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    if (ctx) ctx->last_error = buf;
+    ctx->last_error = buf;
     return st;
 }
 
@@ -56,6 +58,14 @@ inline perks_status use_device(perks_context *ctx) {
     (void)cudaGetLastError();
     return PERKS_OK;
 }
+
+// Raises the dynamic shared memory limit of kernel `fn` on the context's
+// device (which must be current) to the device's opt-in maximum less the
+// kernel's static shared memory, and returns that budget in *budget.
+// cudaFuncSetAttribute acts on the current device only, so the call is made
+// once per (kernel, device) and recorded in a fixed-size table under a mutex
+// (no heap use; safe from several host threads).
+perks_status smem_optin(perks_context *ctx, const void *fn, int *budget);
 
 inline size_t dtype_size(int dtype) {
     return dtype == PERKS_F64 ? 8 : dtype == PERKS_F32 ? 4 : 2;

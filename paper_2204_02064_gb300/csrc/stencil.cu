@@ -4,6 +4,7 @@
 // points perks_stencil_*.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -233,14 +234,10 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
                     "no %s kernel for this dtype/shape/extent (bf16 needs nx divisible by 8)",
                     per_step ? "per-step" : "persistent");
     KernelEntry &k = *kp;
-    if (!k.configured) {
-        cudaFuncAttributes fa;
-        PERKS_CUDA(ctx, cudaFuncGetAttributes(&fa, (const void *)k.fn));
-        k.smem_budget = ctx->smem_optin - (int)fa.sharedSizeBytes;
-        PERKS_CUDA(ctx, cudaFuncSetAttribute((const void *)k.fn,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             k.smem_budget));
-        k.configured = true;
+    int smem_budget = 0;
+    {
+        perks_status rc = smem_optin(ctx, (const void *)k.fn, &smem_budget);
+        if (rc) return rc;
     }
     const int R = sh.radius;
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
@@ -252,7 +249,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
         for (HX = std::max(V, 2); HX < RX; HX += V) {}
     int per_sm = 0;
     PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, k.nt,
-                                                                  k.smem_budget));
+                                                                  smem_budget));
     if (per_sm < 1)
         return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "persistent kernel cannot be resident");
     const int maxG = per_sm * ctx->sm_count;
@@ -278,7 +275,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
             if (nring > k.nt) continue;
             const int PW = txmax + 2 * HX, PH = tymax + 2 * RY;
             const long long ring_bytes = (long long)S * PW * PH * es;
-            if (ring_bytes > k.smem_budget) continue;
+            if (ring_bytes > smem_budget) continue;
             int ntz;
             if (st->has_plan && st->plan.tiles_z > 0) ntz = st->plan.tiles_z;
             else ntz = std::min(Z / std::max(RZ, 1), maxG / (ntx * nty));
@@ -306,7 +303,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     bp.ncol = bp.txmax * bp.tymax;
     bp.blocks = bp.ntx * bp.nty * bp.ntz;
     const long long ring_bytes = (long long)S * bp.plane * es;
-    long long zs = (k.smem_budget - ring_bytes) / ((long long)bp.ncol * es);
+    long long zs = (smem_budget - ring_bytes) / ((long long)bp.ncol * es);
     zs = std::min<long long>(zs, std::max(0, bp.tzmax - k.zr));
     if (st->has_plan && st->plan.smem_cache_planes >= 0) zs = std::min<long long>(zs, st->plan.smem_cache_planes);
     if (per_step) zs = 0;
@@ -888,19 +885,23 @@ constexpr size_t kNoallocScratchBytes = kNoallocHeaderBytes + kNoallocFieldBytes
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kNoallocMaxDevices = 64;
-unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {};
+std::atomic<unsigned char *> g_noalloc_addr[kNoallocMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, not a device address).
+// per device (the host-side symbol is only a stand-in, not a device address)
+// and kept for the life of the process; several host threads may race to
+// store it, which is harmless (they store the same address).
 cudaError_t noalloc_scratch(int device, unsigned char **out) {
     if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_noalloc_addr[device]) {
+    unsigned char *a = g_noalloc_addr[device].load(std::memory_order_acquire);
+    if (!a) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_addr[device] = static_cast<unsigned char *>(p);
+        a = static_cast<unsigned char *>(p);
+        g_noalloc_addr[device].store(a, std::memory_order_release);
     }
-    *out = g_noalloc_addr[device];
+    *out = a;
     return cudaSuccess;
 }
 
@@ -942,6 +943,8 @@ extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc
             if (v < -d.radius || v > d.radius || (a == 2 && d.ndim == 2 && v != 0)) return PERKS_ERR_INVALID_ARG;
         }
     if (d.dtype != PERKS_F64 && d.dtype != PERKS_F32) return PERKS_ERR_UNSUPPORTED;
+    // each extent is checked before the product is formed (no overflow)
+    if (d.nx > kNoallocMaxCells || d.ny > kNoallocMaxCells || d.nz > kNoallocMaxCells) return PERKS_ERR_INVALID_ARG;
     const long long cells = d.nx * d.ny * d.nz;
     if (cells > kNoallocMaxCells) return PERKS_ERR_INVALID_ARG;  // beyond the scratch field's capacity
     cudaStream_t s = (cudaStream_t)stream;
@@ -960,6 +963,7 @@ extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc
 
     // device facts and a stencil description on the stack: nothing is allocated
     perks_context ctx;
+    ctx.quiet = true;  // nothing is formatted or stored for a message
     ctx.device = device;
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PERKS_ERR_CUDA;

@@ -32,8 +32,6 @@ struct KernelEntry {
     int nt = 0, zr = 0, d = 0;
     int v = 1;              // cells per thread along x (1: scalar kernel)
     int p = 2;              // planes per block barrier (vectorised kernel)
-    bool configured = false;
-    int smem_budget = 0;    // dynamic shared memory available per block
 };
 
 void register_vec_f64_core(std::vector<KernelEntry> &out);

@@ -37,3 +37,19 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(src), f
+
+
+def test_noalloc_rejects_overflowing_extents_before_gpu_work():
+    """perks_stencil_run_noalloc checks each extent before forming their
+    product: 2^32 x 2^32 cells (whose product overflows int64 arithmetic on
+    the way) is refused with INVALID_ARG by argument checks alone, before
+    any CUDA call, so it runs without a GPU."""
+    import ctypes as C
+    from paper_2204_02064_gb300 import api, inputs
+    lib = api.load()
+    for shape in [(2 ** 32, 2 ** 32), (1, 2 ** 40, 2 ** 40), (2 ** 21, 1, 1)]:
+        d = api._stencil_desc(shape, inputs.shape_offsets("3d7pt" if len(shape) == 3 else "2d5pt"),
+                              [0.1] * (7 if len(shape) == 3 else 5), "f64", 0.0, None)
+        dummy = C.c_void_p(16)     # never dereferenced: the call fails before using it
+        st = lib.perks_stencil_run_noalloc(C.byref(d), dummy, dummy, 3, C.c_void_p(0), 1)
+        assert api.STATUS[st] == "INVALID_ARG", shape
