@@ -96,6 +96,14 @@ perks_status perks_context_set_barrier_timeout(perks_context *ctx, int64_t limit
 perks_status perks_barrier_benchmark(perks_context *ctx, int32_t blocks, int32_t threads,
                                      int32_t iterations, double *us_per_barrier);
 
+/* FP64 pipe throughput (a measurement aid, not in the paper): times one
+ * launch (after a warm-up launch) of 4 blocks of 256 threads per SM, each
+ * thread running eight independent chains of `iterations` fp64 fused
+ * multiply-adds, and returns the rate in TFLOP/s (2 FLOP per FMA).  The
+ * ceiling of stencils whose fp64 arithmetic, not memory, bounds a step.
+ * Errors: INVALID_ARG, CUDA. */
+perks_status perks_fp64_fma_benchmark(perks_context *ctx, int32_t iterations, double *tflops);
+
 /* Device facts used by planners and reports: SM count, opt-in shared memory
  * per block (bytes), L2 size (bytes).  Any out pointer may be NULL. */
 perks_status perks_context_info(const perks_context *ctx, int32_t *sm_count,
@@ -134,7 +142,12 @@ typedef struct {
     int32_t reserved[4];                /* reserved[0] = 1: one-cell-per-thread kernel instead of
                                            the 16-byte-vector kernel; reserved[1] = planes per
                                            block barrier of the vector kernel (2 or 4, 0 =
-                                           automatic); others must be 0 */
+                                           automatic); reserved[2] = kernel body
+                                           (PERKS_KERNEL_AUTO / _RESIDENT / _STREAMING; AUTO in a
+                                           plan means STREAMING, AUTO with no plan picks the
+                                           resident tile when every tile fits in shared memory);
+                                           reserved[3] = threads per block of the resident
+                                           tile kernel (256, 512 or 1024; 0 = automatic) */
 } perks_stencil_plan;
 
 /* What a run did; filled by perks_stencil_run when asked. */
@@ -150,7 +163,21 @@ typedef struct {
     int64_t cached_cells;               /* cells held on chip between steps (D_cache) */
     int64_t halo_cells_per_step;        /* halo cells written + read per step (H) */
     double algorithmic_bytes;           /* S (2 N D_uncache + 2 D_cache) + S N H for the whole run */
+    int32_t kernel;                     /* PERKS_KERNEL_*: which kernel body runs */
+    int32_t planes_per_sync;            /* resident tile: planes a thread computes between two block
+                                           barriers; plane streaming: planes per block barrier */
 } perks_run_stats;
+
+/* Kernel bodies of a stencil run (perks_run_stats.kernel, perks_stencil_plan.reserved[2]). */
+enum {
+    PERKS_KERNEL_AUTO = 0,       /* plan field only: choose automatically */
+    PERKS_KERNEL_RESIDENT = 1,   /* resident tile: every block keeps its whole tile in shared memory
+                                    for all steps (radius-1 stars: 2d5pt, 3d7pt) */
+    PERKS_KERNEL_STREAMING = 2,  /* plane streaming: a block walks its tile plane by plane through a
+                                    shared-memory ring, caching some planes in registers / shared
+                                    memory */
+    PERKS_KERNEL_PER_STEP = 3    /* one launch per step (PERKS_PER_STEP) */
+};
 
 /* Creates a stencil over a device-resident domain described by *desc (the
  * library keeps its own copy of the field, two ping-pong buffers and the halo

@@ -40,9 +40,17 @@
  *
  * Every function here is pinned by tests/test_oracle_*.py against closed
  * forms, invariants and library routines, not against itself.
+ *
+ * A second build of this same file with -fopenmp (the all-cores CPU
+ * baseline of the benchmark, nothing else) runs the planes of each stencil
+ * step in parallel; every cell's sum is computed exactly as in the serial
+ * build, so the results are identical.
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -103,6 +111,9 @@ int oracle_stencil_run(int ndim, int64_t nx, int64_t ny, int64_t nz, int radius,
                    off[3 * o + 0];
 
     for (int64_t s = 0; s < steps; ++s) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t k = 0; k < nz; ++k)
             for (int64_t j = 0; j < ny; ++j)
                 for (int64_t i = 0; i < nx; ++i) {
@@ -584,4 +595,14 @@ done:
     }
     free(r); free(val32); free(rf); free(pf); free(qf); free(df);
     return status;
+}
+
+/* Threads the stencil's parallel loop uses (1 in the serial build). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

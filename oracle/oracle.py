@@ -27,18 +27,54 @@ NOT_CONVERGED = -7
 BREAKDOWN = -8
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into oracle/_build/liboracle.so (plain gcc, no -march)."""
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (plain gcc, no -march);
+    with openmp=True the same source with -fopenmp into liboracle_omp.so
+    (the all-cores CPU baseline of the benchmark only)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
+    so = _SO_OMP if openmp else _SO
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC)):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
            "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def stencil_run_all_cores(field: np.ndarray, offsets, weights, steps: int, boundary: float = 0.0):
+    """oracle_stencil_run from the OpenMP build (planes of a step in parallel
+    on every host core; identical results).  Returns (field, threads)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build(openmp=True))
+            P = ctypes.c_void_p
+            i64, f64 = ctypes.c_int64, ctypes.c_double
+            lib.oracle_stencil_run.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_int,
+                                               ctypes.c_int, P, P, f64, i64, P, P]
+            lib.oracle_stencil_run.restype = ctypes.c_int
+            lib.oracle_threads.restype = ctypes.c_int
+            _lib_omp = lib
+    lib = _lib_omp
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    dims = list(f.shape[::-1]) + [1, 1, 1]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    out = np.empty_like(f)
+    st = lib.oracle_stencil_run(f.ndim, dims[0], dims[1], dims[2], int(np.abs(off).max()), off.shape[0],
+                                _ptr(off), _ptr(w), float(boundary), int(steps), _ptr(f), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_stencil_run failed with status {st}")
+    return out, int(lib.oracle_threads())
 
 
 def _load():

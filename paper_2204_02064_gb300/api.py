@@ -18,6 +18,8 @@ from . import build as _build
 MAX_POINTS = 125
 F64, F32, BF16 = 0, 1, 2
 PERSISTENT, PER_STEP = 0, 1
+KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_STREAMING, KERNEL_PER_STEP = 0, 1, 2, 3
+KERNEL_NAMES = {KERNEL_RESIDENT: "resident", KERNEL_STREAMING: "streaming", KERNEL_PER_STEP: "per_step"}
 CG_FP64, CG_FP32_IR, CG_FP64_MULTI = 0, 1, 2
 SPMV_ROWVEC, SPMV_MERGE, SPMV_SEG = 0, 1, 2
 
@@ -58,7 +60,8 @@ class RunStats(ctypes.Structure):
                 ("smem_cache_planes", ctypes.c_int32), ("prefetch_planes", ctypes.c_int32),
                 ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
                 ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
-                ("algorithmic_bytes", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_double), ("kernel", ctypes.c_int32),
+                ("planes_per_sync", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,7 +84,8 @@ class BatchStats(ctypes.Structure):
                 ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
                 ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
                 ("granularity", ctypes.c_double), ("predicted_ms_per_step", ctypes.c_double),
-                ("algorithmic_bytes", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_double), ("kernel", ctypes.c_int32),
+                ("planes_per_sync", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +129,7 @@ def _declare(lib):
                             ctypes.POINTER(CgStats)], i32),
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
+        "perks_fp64_fma_benchmark": ([P, i32, ctypes.POINTER(f64)], i32),
         "perks_op_set_spmv": ([P, i32], i32),
         "perks_op_set_vector_cache": ([P, i32], i32),
         "perks_op_vector_cache_active": ([P], i32),
@@ -241,6 +246,12 @@ class Context:
                                                      ctypes.byref(us)))
         return us.value
 
+    def fp64_fma_benchmark(self, iterations: int = 20000) -> float:
+        """Measured FP64 pipe throughput in TFLOP/s (independent FMA chains on every SM)."""
+        t = ctypes.c_double()
+        self.check(self._lib.perks_fp64_fma_benchmark(self.handle, int(iterations), ctypes.byref(t)))
+        return t.value
+
     def set_barrier_timeout(self, ns: int):
         self.check(self._lib.perks_context_set_barrier_timeout(self.handle, int(ns)))
 
@@ -337,17 +348,23 @@ class Stencil:
         self.cells = int(np.prod(shape))
 
     def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1,
-                 scalar: bool = False, planes_per_barrier: int = 0):
+                 scalar: bool = False, planes_per_barrier: int = 0, kernel: int = KERNEL_AUTO,
+                 threads: int = 0):
         """Plan override; ``scalar`` selects the one-cell-per-thread kernel
         instead of the 16-byte-vector kernel; ``planes_per_barrier`` (2 or 4,
         0 = automatic) picks how many planes the vector kernel computes
-        between two block barriers."""
+        between two block barriers; ``kernel`` = KERNEL_RESIDENT selects the
+        resident-tile kernel (``tiles`` and ``threads`` 256/512/1024 apply to
+        it, 0 = automatic), KERNEL_STREAMING / KERNEL_AUTO the plane-streaming
+        kernel."""
         p = StencilPlan()
         p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
         p.smem_cache_planes = int(smem_cache_planes)
         p.reg_cache = int(reg_cache)
         p.reserved[0] = 1 if scalar else 0
         p.reserved[1] = int(planes_per_barrier)
+        p.reserved[2] = int(kernel)
+        p.reserved[3] = int(threads)
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
 
     def autotune(self, variant: int = PERSISTENT, probe_steps: int = 10, stream=None) -> dict:
@@ -359,6 +376,7 @@ class Stencil:
                                                         _stream(stream), ctypes.byref(p), ctypes.byref(ms)))
         return {"tiles": (p.tiles_x, p.tiles_y, p.tiles_z), "reg_cache": p.reg_cache,
                 "smem_cache_planes": p.smem_cache_planes, "planes_per_barrier": p.reserved[1],
+                "kernel": KERNEL_NAMES.get(p.reserved[2], "streaming"), "threads": p.reserved[3],
                 "ms_per_step": ms.value}
 
     def set_trace(self, steps: int):

@@ -60,7 +60,50 @@ __global__ void barrier_bench_kernel(unsigned long long *counter, DevError *err,
         if (!grid_barrier(counter, gridDim.x, epoch, err, timeout_ns)) return;
 }
 
+// Eight independent fused multiply-add chains per thread, `iters` long: with
+// 32 warps per SM enough FMAs are in flight to keep the FP64 pipe busy, so
+// the rate measured is the pipe's throughput.  b < 1 and c keep every value
+// bounded; the sums are written out so that no chain is dead code.
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double *out, int iters, double b, double c) {
+    const double s = 1e-9 * (threadIdx.x + 1);
+    double a0 = s, a1 = 2 * s, a2 = 3 * s, a3 = 4 * s, a4 = 5 * s, a5 = 6 * s, a6 = 7 * s, a7 = 8 * s;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+
 }  // namespace
+
+extern "C" perks_status perks_fp64_fma_benchmark(perks_context *ctx, int32_t iterations, double *tflops) {
+    if (!ctx) return PERKS_ERR_INVALID_ARG;
+    if (iterations < 1 || !tflops) return fail(ctx, PERKS_ERR_INVALID_ARG, "fp64_fma_benchmark: bad arguments");
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    const int threads = 256, blocks = 4 * ctx->sm_count;
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(double) * threads * blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+        if (e == cudaSuccess) e = cudaEventRecord(e0);
+        fp64_fma_kernel<<<blocks, threads>>>(out, iterations, 0.9999999, 1e-7);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fp64_fma_benchmark");
+    const double flop = 2.0 * 8.0 * (double)iterations * threads * blocks;
+    *tflops = flop / (ms * 1e-3) / 1e12;
+    return PERKS_OK;
+}
 
 extern "C" perks_status perks_context_create(int device, perks_context **out) {
     if (!out) return PERKS_ERR_INVALID_ARG;

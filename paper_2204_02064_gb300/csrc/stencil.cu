@@ -11,6 +11,7 @@
 
 #include "internal.h"
 #include "stencil_registry.h"
+#include "stencil_tile.cuh"
 
 using namespace perks;
 
@@ -73,11 +74,9 @@ KernelEntry entry(int dtype, int shape) {
     return e;
 }
 
-std::vector<KernelEntry> &registry() {
-    static std::vector<KernelEntry> table;
-    static bool init = false;
-    if (!init) {
-        init = true;
+std::vector<KernelEntry> build_registry() {
+    std::vector<KernelEntry> table;
+    {
         // scalar kernels: any x extent (fp64 / fp32)
         table.push_back(entry<double, S2d5, 256, 0>(PERKS_F64, SH_2D5));
         table.push_back(entry<double, S2d5, 256, 16>(PERKS_F64, SH_2D5));
@@ -115,6 +114,20 @@ std::vector<KernelEntry> &registry() {
     return table;
 }
 
+std::vector<KernelEntry> &registry() {
+    static std::vector<KernelEntry> table = build_registry();  // built once, thread-safe
+    return table;
+}
+
+std::vector<TileKernelEntry> &tile_registry() {
+    static std::vector<TileKernelEntry> table = [] {
+        std::vector<TileKernelEntry> t;
+        register_tile_kernels(t);
+        return t;
+    }();
+    return table;
+}
+
 // Planes per block barrier preferred by default where both variants exist.
 constexpr int kDefaultPlanesPerBarrier = 2;
 
@@ -147,6 +160,12 @@ struct Plan {
     int blocks = 0;
     long long cached_cells = 0;
     long long halo_cells = 0;  // per step
+    // resident-tile kernel (the whole tile in shared memory): tiles ntx x nty x ntz of
+    // tx x tymax x tzmax cells at most
+    bool resident = false;
+    TileKernelEntry *tk = nullptr;
+    int tx = 0, PP = 0, XGS = 0, groups = 0, chunks = 0;
+    long long FS = 0;
 };
 
 }  // namespace
@@ -171,6 +190,9 @@ struct perks_stencil {
     perks_stencil_plan plan{};
     unsigned long long *trace = nullptr;  // optional step trace of the persistent kernel
     int trace_steps = 0, trace_blocks = 0, trace_grid = 0;
+    void *tfaces[2] = {nullptr, nullptr};  // resident-tile kernel: face buffers by step parity
+    size_t tfaces_bytes = 0;
+    bool no_resident = false;             // plan the plane-streaming kernel only
 };
 
 namespace {
@@ -201,8 +223,112 @@ int match_shape(const perks_stencil_desc &d, double *kw) {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Plan of the resident-tile kernel: the tiling (one block per SM at most)
+// whose tiles fit in shared memory with their ghost cells and that needs the
+// fewest plane slots per thread and step.  Modelled cost of a step, in units
+// of one 16-byte vector handled by one thread: slots * threads (dummy slots
+// of uneven segments included) + half a slot per block barrier + the ghost
+// vectors copied in.  Tiles split x exactly into rows of 1..32 vectors (a
+// warp holds whole rows), y and z into nearly equal parts.
+perks_status make_tile_plan(perks_stencil *st, Plan &pl) {
+    perks_context *ctx = st->ctx;
+    if (st->shape_id != SH_2D5 && st->shape_id != SH_3D7)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED, "resident-tile kernel: compiled for the 2d5pt and 3d7pt stencils only");
+    const bool fixed = st->has_plan && st->plan.reserved[2] == PERKS_KERNEL_RESIDENT;
+    const int want_nt = fixed ? st->plan.reserved[3] : 0;
+    const int fx = fixed ? st->plan.tiles_x : 0, fy = fixed ? st->plan.tiles_y : 0, fz = fixed ? st->plan.tiles_z : 0;
+    const int GY = shape_by_id(st->shape_id).ndim == 3 ? 1 : 0;
+    const int X = st->X, Y = st->Y, Z = st->Z, es = st->es;
+    const int maxG = ctx->sm_count;
+    double best = 1e300;
+    Plan bp;
+    long long best_smem = 0;
+    for (TileKernelEntry &e : tile_registry()) {
+        if (e.dtype != st->desc.dtype || e.shape != st->shape_id) continue;
+        if (want_nt > 0 && e.nt != want_nt) continue;
+        const int V = e.v;
+        if (X % V != 0) continue;
+        int budget = 0;
+        const perks_status rc = smem_optin(ctx, (const void *)e.fn, &budget);
+        if (rc) return rc;
+        const int XV = X / V;
+        for (int ntx = 1; ntx <= XV; ++ntx) {
+            if ((fx > 0 && ntx != fx) || XV % ntx != 0) continue;
+            const int nvx = XV / ntx, tx = nvx * V;
+            if (nvx > 32 || 32 % nvx != 0) continue;
+            for (int nty = 1; nty <= Y && ntx * nty <= maxG; ++nty) {
+                if (fy > 0 && nty != fy) continue;
+                const int tymax = ceil_div(Y, nty);
+                if (fy == 0 && nty > 1 && tymax == ceil_div(Y, nty - 1)) continue;  // same tiles, more of them
+                const int P = nvx * tymax;
+                if (P > e.nt) continue;
+                const int G = e.nt / P;
+                const int ntz = fz > 0 ? fz : std::min(Z, maxG / (ntx * nty));
+                if (ntz < 1 || ntz > Z || (long long)ntx * nty * ntz > maxG) continue;
+                const int tzmax = ceil_div(Z, ntz);
+                const int XGS = round_up(tzmax * tymax, V);
+                const int PP = (tymax + 2 * GY) * tx;
+                const long long smem = ((long long)(tzmax + 2) * PP + 2LL * XGS) * es;
+                if (smem > budget) continue;
+                const int L = ceil_div(tzmax, G), C = ceil_div(L, e.m);
+                const double ghosts = 2.0 * tymax * nvx + (GY ? 2.0 * tzmax * nvx : 0.0) + 2.0 * XGS / V;
+                const double cost = (double)C * e.m * e.nt + 0.5 * C * e.nt + ghosts;
+                if (cost < best) {
+                    best = cost;
+                    bp.tk = &e;
+                    bp.ntx = ntx; bp.nty = nty; bp.ntz = ntz;
+                    bp.tx = tx; bp.txmax = tx; bp.tymax = tymax; bp.tzmax = tzmax;
+                    bp.PP = PP; bp.XGS = XGS; bp.groups = G; bp.chunks = C;
+                    best_smem = smem;
+                }
+            }
+        }
+    }
+    if (!bp.tk)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                    "resident-tile kernel: no tiling of %dx%dx%d fits shared memory on %d blocks", X, Y, Z, maxG);
+    bp.resident = true;
+    bp.blocks = bp.ntx * bp.nty * bp.ntz;
+    bp.smem = best_smem;
+    bp.FS = 2LL * bp.XGS + 2LL * bp.tzmax * bp.tx + 2LL * bp.tymax * bp.tx;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)bp.tk->fn, bp.tk->nt,
+                                                                  (size_t)bp.smem));
+    if ((long long)per_sm * ctx->sm_count < bp.blocks)
+        return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "resident-tile kernel: %d blocks are not co-resident", bp.blocks);
+    // halo cells written + read per step
+    long long halo = 0;
+    for (int t = 0; t < bp.blocks; ++t) {
+        const int ti = t % bp.ntx, tj = (t / bp.ntx) % bp.nty, tk = t / (bp.ntx * bp.nty);
+        int y0, ty, z0, tz;
+        split_axis(Y, bp.nty, tj, y0, ty);
+        split_axis(Z, bp.ntz, tk, z0, tz);
+        const int nfx = (ti > 0) + (ti + 1 < bp.ntx), nfy = (tj > 0) + (tj + 1 < bp.nty);
+        const int nfz = (tk > 0) + (tk + 1 < bp.ntz);
+        halo += 2LL * ((long long)nfx * ty * tz + (GY ? (long long)nfy * bp.tx * tz : 0) + (long long)nfz * bp.tx * ty);
+    }
+    bp.cached_cells = st->cells;
+    bp.halo_cells = halo;
+    bp.plane = 0;
+    bp.zs = bp.tzmax;
+    pl = bp;
+    return PERKS_OK;
+}
+
 perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     perks_context *ctx = st->ctx;
+    // The resident-tile kernel when it is asked for, or by default (no plan)
+    // when every tile of the domain fits in shared memory.
+    const int kind = st->has_plan ? st->plan.reserved[2] : PERKS_KERNEL_AUTO;
+    if (!per_step && !st->no_resident && st->shape_id >= 0 &&
+        (kind == PERKS_KERNEL_RESIDENT || (!st->has_plan && kind == PERKS_KERNEL_AUTO))) {
+        const std::string saved_msg = ctx->last_error;
+        const perks_status rc = make_tile_plan(st, pl);
+        if (rc == PERKS_OK || kind == PERKS_KERNEL_RESIDENT) return rc;
+        ctx->last_error = saved_msg;
+    }
     if (st->shape_id < 0)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
                     "persistent kernel: offsets do not match a compiled shape "
@@ -364,7 +490,22 @@ void fill_stats(const perks_stencil *st, const Plan *pl, long long steps, int va
     o->variant = variant;
     o->cells = st->cells;
     const double S = st->es;
-    if (variant == PERKS_PERSISTENT && pl) {
+    if (variant == PERKS_PERSISTENT && pl && pl->resident) {
+        o->kernel = PERKS_KERNEL_RESIDENT;
+        o->grid_blocks = pl->blocks;
+        o->threads_per_block = pl->tk->nt;
+        o->tiles_x = pl->ntx; o->tiles_y = pl->nty; o->tiles_z = pl->ntz;
+        o->reg_cache_planes = 0;
+        o->smem_cache_planes = pl->tzmax;
+        o->prefetch_planes = 0;
+        o->planes_per_sync = pl->tk->m;
+        o->smem_bytes_per_block = pl->smem;
+        o->cached_cells = st->cells;
+        o->halo_cells_per_step = pl->halo_cells;
+        o->algorithmic_bytes = steps > 0 ? S * (2.0 * (double)st->cells + (double)steps * pl->halo_cells) : 0.0;
+    } else if (variant == PERKS_PERSISTENT && pl) {
+        o->kernel = PERKS_KERNEL_STREAMING;
+        o->planes_per_sync = pl->k->p;
         o->grid_blocks = pl->blocks;
         o->threads_per_block = pl->k->nt;
         o->tiles_x = pl->ntx; o->tiles_y = pl->nty; o->tiles_z = pl->ntz;
@@ -378,9 +519,70 @@ void fill_stats(const perks_stencil *st, const Plan *pl, long long steps, int va
         o->algorithmic_bytes = steps > 0 ? S * (2.0 * steps * dun + 2.0 * pl->cached_cells +
                                                 (double)steps * pl->halo_cells) : 0.0;
     } else {
+        o->kernel = PERKS_KERNEL_PER_STEP;
         o->threads_per_block = 256;
         o->algorithmic_bytes = S * 2.0 * (double)steps * (double)st->cells;
     }
+}
+
+perks_status ensure_tile_buffers(perks_stencil *st, const Plan &pl) {
+    perks_context *ctx = st->ctx;
+    const size_t need = (size_t)pl.blocks * (size_t)pl.FS * st->es;
+    if (need > st->tfaces_bytes) {
+        for (int i = 0; i < 2; ++i) {
+            if (st->tfaces[i]) cudaFree(st->tfaces[i]);
+            st->tfaces[i] = nullptr;
+        }
+        st->tfaces_bytes = 0;
+        for (int i = 0; i < 2; ++i) PERKS_CUDA(ctx, cudaMalloc(&st->tfaces[i], need));
+        st->tfaces_bytes = need;
+    }
+    if (!st->bar) PERKS_CUDA(ctx, cudaMalloc(&st->bar, sizeof(unsigned long long)));
+    if (!st->err) PERKS_CUDA(ctx, cudaMalloc(&st->err, sizeof(DevError)));
+    return PERKS_OK;
+}
+
+// One cooperative launch of the resident-tile kernel: reads field[cur] before
+// the first step, writes field[cur ^ (steps & 1)] after the last (the same
+// buffer when steps is even: every block has read its tile before any block
+// passes the first grid barrier).
+perks_status run_resident(perks_stencil *st, long long steps, cudaStream_t s, const Plan &pl) {
+    perks_context *ctx = st->ctx;
+    perks_status rc = ensure_tile_buffers(st, pl);
+    if (rc) return rc;
+    TileArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = st->X; a.Y = st->Y; a.Z = st->Z;
+    a.XY = (long long)st->X * st->Y;
+    a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
+    a.tx = pl.tx; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
+    a.PP = pl.PP; a.XGS = pl.XGS; a.FS = pl.FS;
+    a.groups = pl.groups; a.chunks = pl.chunks;
+    a.steps = steps;
+    a.boundary = st->desc.boundary;
+    a.boundary_f = (float)st->desc.boundary;
+    for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
+    a.in = st->field[st->cur];
+    a.out = st->field[st->cur ^ (int)(steps & 1)];
+    a.faces[0] = st->tfaces[0];
+    a.faces[1] = st->tfaces[1];
+    a.bar = st->bar;
+    a.err = st->err;
+    a.timeout_ns = ctx->timeout_ns;
+    if (st->trace && pl.blocks <= st->trace_blocks) {
+        a.trace = st->trace;
+        a.trace_steps = st->trace_steps;
+        st->trace_grid = pl.blocks;
+        PERKS_CUDA(ctx, cudaMemsetAsync(st->trace, 0, sizeof(unsigned long long) * 2 * (size_t)(st->trace_steps + 1) *
+                                                          st->trace_blocks, s));
+    }
+    PERKS_CUDA(ctx, cudaMemsetAsync(st->bar, 0, sizeof(unsigned long long), s));
+    PERKS_CUDA(ctx, cudaMemsetAsync(st->err, 0, sizeof(DevError), s));
+    void *args[] = {&a};
+    PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)pl.tk->fn, dim3(pl.blocks), dim3(pl.tk->nt), args,
+                                                (size_t)pl.smem, s));
+    if (steps & 1) st->cur ^= 1;
+    return PERKS_OK;
 }
 
 perks_status ensure_persistent_buffers(perks_stencil *st, const Plan &pl) {
@@ -436,6 +638,7 @@ perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, 
     perks_context *ctx = st->ctx;
     perks_status rc = make_plan(st, pl);
     if (rc) return rc;
+    if (pl.resident) return run_resident(st, steps, s, pl);
     rc = ensure_persistent_buffers(st, pl);
     if (rc) return rc;
     int per_sm = 0;
@@ -579,6 +782,8 @@ extern "C" perks_status perks_stencil_destroy(perks_stencil *st) {
         if (st->field[i]) cudaFree(st->field[i]);
         if (st->faces[i]) cudaFree(st->faces[i]);
     }
+    for (int i = 0; i < 2; ++i)
+        if (st->tfaces[i]) cudaFree(st->tfaces[i]);
     if (st->bar) cudaFree(st->bar);
     if (st->err) cudaFree(st->err);
     if (st->trace) cudaFree(st->trace);
@@ -622,8 +827,10 @@ extern "C" perks_status perks_stencil_set_plan(perks_stencil *st, const perks_st
         return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: negative field");
     if (plan->reserved[1] != 0 && plan->reserved[1] != 2 && plan->reserved[1] != 4)
         return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: planes per barrier must be 0, 2 or 4");
-    if (plan->reserved[2] != 0 || plan->reserved[3] != 0)
-        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: reserved fields must be 0");
+    if (plan->reserved[2] < PERKS_KERNEL_AUTO || plan->reserved[2] > PERKS_KERNEL_STREAMING)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: kernel must be AUTO, RESIDENT or STREAMING");
+    if (plan->reserved[3] != 0 && plan->reserved[3] != 256 && plan->reserved[3] != 512 && plan->reserved[3] != 1024)
+        return fail(st->ctx, PERKS_ERR_INVALID_ARG, "stencil_set_plan: threads must be 0, 256, 512 or 1024");
     st->plan = *plan;
     st->has_plan = true;
     return PERKS_OK;
@@ -789,8 +996,29 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
     const perks_stencil_plan saved_plan = st->plan;
     st->has_plan = false;
     Plan base;
+    const bool had_no_resident = st->no_resident;
+    st->no_resident = true;  // the plane-streaming kernel's own tiling
     rc = make_plan(st, base, per_step);
+    st->no_resident = had_no_resident;
     if (rc) { st->has_plan = had_plan; st->plan = saved_plan; return rc; }
+    // resident-tile candidates first (their tiling from the planner), one per thread count
+    if (!per_step && !st->no_resident)
+        for (int nt : {256, 512, 1024}) {
+            perks_stencil_plan p{};
+            p.smem_cache_planes = -1;
+            p.reserved[2] = PERKS_KERNEL_RESIDENT;
+            p.reserved[3] = nt;
+            st->plan = p;
+            st->has_plan = true;
+            Plan probe;
+            const std::string saved_msg = ctx->last_error;
+            if (make_plan(st, probe, false) == PERKS_OK) {
+                p.tiles_x = probe.ntx; p.tiles_y = probe.nty; p.tiles_z = probe.ntz;
+                plans.push_back(p);
+            }
+            ctx->last_error = saved_msg;
+        }
+    st->has_plan = false;
     std::vector<std::array<int, 3>> tilings = {{base.ntx, base.nty, base.ntz}};
     for (const TileCand &c : tile_candidates(st, per_step, 6))
         if (!(c.ntx == base.ntx && c.nty == base.nty && c.ntz == base.ntz)) tilings.push_back({c.ntx, c.nty, c.ntz});
@@ -981,6 +1209,7 @@ extern "C" perks_status perks_stencil_run_noalloc(const perks_stencil_desc *desc
     st.cells = cells;
     st.shape_id = match_shape_noalloc(d, st.kw);
     if (st.shape_id < 0) return PERKS_ERR_UNSUPPORTED;
+    st.no_resident = true;  // the scratch layout below is the plane-streaming kernel's
     Plan pl;
     perks_status rc = make_plan(&st, pl);
     if (rc) return rc;

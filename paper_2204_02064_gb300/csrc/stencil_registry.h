@@ -48,4 +48,7 @@ void register_vec_f32_poisson(std::vector<KernelEntry> &out);
 void register_vec_bf16_poisson(std::vector<KernelEntry> &out);
 void register_vec_star2d_hi(std::vector<KernelEntry> &out);
 
+struct TileKernelEntry;  // stencil_tile.cuh
+void register_tile_kernels(std::vector<TileKernelEntry> &out);
+
 }  // namespace perks
