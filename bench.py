@@ -133,9 +133,10 @@ def replica_throughput(world, units_per_rank, total_ms):
     return world * units_per_rank / (total_ms * 1e-3)
 
 
-def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1, tune=True):
+def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1, tune=True, keep_result=False):
     """Times K runs of `steps` Jacobi steps (plan chosen by the autotuner for
-    this variant first); returns dict with per-run ms."""
+    this variant first); returns dict with per-run ms (and the field after
+    the last run, as float64 on the device, when keep_result)."""
     from paper_2204_02064_gb300 import inputs
     shape = (L, L, L)
     f = torch.from_numpy(inputs.stencil_field(shape, seed)).to(
@@ -163,8 +164,27 @@ def stencil_leg(api, torch, ctx, L, steps, dtype, variant, K, W, seed=1, tune=Tr
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     st.check()
+    result = None
+    if keep_result:
+        out = torch.empty_like(f)
+        st.get_field(out)
+        result = out.double()
     st.close()
-    return {"ms": times, "desc": desc, "cells": L ** 3, "plan": tuned}
+    return {"ms": times, "desc": desc, "cells": L ** 3, "plan": tuned, "result": result}
+
+
+def field_error(torch, got, ref):
+    """Error of a field against a reference field (both float64 on the
+    device): max |g - r| / max |r|, and the normwise-per-element error of the
+    parity tests, max |g - r| / max(|r|, 1e-3 max |r|)."""
+    d = (got - ref).abs()
+    m = ref.abs().max()
+    floor = torch.clamp(ref.abs(), min=1e-3 * float(m))
+    return {"max_rel_to_max": float(d.max() / m), "normwise": float((d / floor).max())}
+
+
+def kernel_name(desc):
+    return {1: "resident", 2: "streaming", 3: "per_step"}.get(desc.get("kernel"), "unknown")
 
 
 def stencil2d_leg(api, torch, ctx, L, steps, variant, K, W):
@@ -172,7 +192,8 @@ def stencil2d_leg(api, torch, ctx, L, steps, variant, K, W):
     f = torch.from_numpy(inputs.stencil_field((L, L), inputs.SEED_2D)).cuda()
     st = api.Stencil(ctx, (L, L), inputs.shape_offsets("2d5pt"), inputs.workload_weights("2d5pt"))
     st.set_field(f)
-    st.autotune(variant, probe_steps=20)
+    plan = st.autotune(variant, probe_steps=20)
+    kernel = kernel_name(st.describe(steps, variant))
     stream = torch.cuda.current_stream()
     for _ in range(W):
         st.set_field(f)
@@ -189,7 +210,7 @@ def stencil2d_leg(api, torch, ctx, L, steps, variant, K, W):
         times.append(e0.elapsed_time(e1))
     st.check()
     st.close()
-    return times
+    return {"ms": times, "plan": plan, "kernel": kernel}
 
 
 def e2e_leg(api, torch, ctx, L, steps, K, W):
@@ -244,7 +265,7 @@ def cg_leg(api, torch, ctx, K):
             setup_s = time.perf_counter() - t0
             op.solve(b, x, rtol=rtol, mode=mode)     # warm-up
             times, stats = [], None
-            for _ in range(K):
+            for _ in range(K if kind != api.SPMV_SEG else min(K, 3)):
                 x.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -254,12 +275,15 @@ def cg_leg(api, torch, ctx, K):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
                 stats = op.last_result()
-            out[name] = {"ms_to_tol": min(times), "rtol": rtol, "iters": stats["iterations"], "spmv": kind,
+            med = statistics.median(times)
+            out[name] = {"ms_to_tol": med, "ms_min": min(times), "ms_max": max(times),
+                         "ms_stdev": statistics.stdev(times) if len(times) > 1 else 0.0, "runs": len(times),
+                         "rtol": rtol, "iters": stats["iterations"], "spmv": kind,
                          "set_spmv_s": setup_s,
                          "outer": stats["outer_iterations"],
                          "true_rel_residual": stats["true_rel_residual"],
                          "sustained_gbs": stats["bytes_per_iteration"] * stats["iterations"]
-                         / (min(times) * 1e-3) / 1e9}
+                         / (med * 1e-3) / 1e9}
         except Exception as e:  # report, do not hide
             out[name] = {"error": str(e)}
     op.close()
@@ -298,11 +322,37 @@ def batch_leg(api, torch, ctx, K):
         ms = min(times)
         out[name] = {"ms": ms, "gcells": cells * 500 / (ms * 1e-3) / 1e9}
     b.close()
+    # the honest alternative: the 64 domains back to back, each through the
+    # single-domain persistent path with its own autotuned plan
+    sts = []
+    for j, d in enumerate(doms):
+        st = api.Stencil(ctx, d["shape"], d["offsets"], d["weights"], dtype="f32")
+        st.set_field(fields[j])
+        st.autotune(api.PERSISTENT, probe_steps=10)
+        sts.append(st)
+    times = []
+    for i in range(K + 1):
+        for j, st in enumerate(sts):
+            st.set_field(fields[j])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for st in sts:
+            st.run(500)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            times.append(e0.elapsed_time(e1))
+    for st in sts:
+        st.check()
+        st.close()
+    ms = min(times)
+    out["sequential_persistent"] = {"ms": ms, "gcells": cells * 500 / (ms * 1e-3) / 1e9}
     return out
 
 
 def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=8, batch=16, lr=1e-3,
-                  label_rtol=1e-6, max_iter=100000, pool=4):
+                  label_rtol=1e-6, max_iter=100000, pool=4, reps=2):
     """The variable-coefficient Poisson workload: 256 problems on 512^2
     grids, k = exp(GRF, length 32, sigma 1), f uniform[-1,1), Dirichlet 0;
     CG to 1e-8 from zero vs from the BF16 warm-start network (inference
@@ -349,8 +399,8 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=8, bat
     x = torch.zeros_like(f)
     u0 = torch.zeros_like(f)
     res = {"zero": {"ms_runs": []}, "warm": {"ms_runs": [], "inference_ms": []}}
-    for rep in range(2):  # alternate the two starts, twice
-        for name in ("zero", "warm") if rep == 0 else ("warm", "zero"):
+    for rep in range(reps):  # alternate the two starts
+        for name in ("zero", "warm") if rep % 2 == 0 else ("warm", "zero"):
             x.zero_()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -372,12 +422,17 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=8, bat
         if name == "warm":
             net.predict(k, f, x)
         stats = P.solve(f, x, rtol=1e-8, max_iter=max_iter)
-        res[name].update({"ms_to_tol": min(res[name]["ms_runs"]), "mean_iterations": stats["mean_iterations"],
+        runs = res[name]["ms_runs"]
+        res[name].update({"ms_to_tol": statistics.median(runs), "ms_min": min(runs), "ms_max": max(runs),
+                          "mean_iterations": stats["mean_iterations"],
                           "max_iterations": stats["max_iterations"],
                           "max_true_rel_residual": stats["max_true_rel_residual"]})
     res["warm"]["inference_ms"] = min(res["warm"]["inference_ms"])
     out.update(res)
     out["speedup"] = res["zero"]["ms_to_tol"] / res["warm"]["ms_to_tol"]
+    # the gain counts only if it exceeds the run-to-run spread of either start
+    out["spread_ms"] = max(res["zero"]["ms_max"] - res["zero"]["ms_min"], res["warm"]["ms_max"] - res["warm"]["ms_min"])
+    out["gain_ms"] = res["zero"]["ms_to_tol"] - res["warm"]["ms_to_tol"]
     P.close()
     net.close()
     return out
@@ -385,7 +440,10 @@ def warmstart_leg(api, torch, ctx, ntrain=10000, nprob=256, n=512, epochs=8, bat
 
 def cpu_baseline_sample(max_seconds=15.0):
     """The oracle on a bounded sample of the workload: the 384^3 3d7pt field
-    for as many whole steps as fit in ~max_seconds (at least one)."""
+    for as many whole steps as fit in ~max_seconds (at least one), timed
+    single-threaded and, from the OpenMP build of the same source (identical
+    results), on every host core.  The all-cores figure is the line's
+    value."""
     from oracle import oracle
     from paper_2204_02064_gb300 import inputs
     f = inputs.stencil_field((L_3D, L_3D, L_3D), 1)
@@ -398,8 +456,15 @@ def cpu_baseline_sample(max_seconds=15.0):
     t0 = time.perf_counter()
     oracle.stencil_run(f, offs, w, steps)
     dt = time.perf_counter() - t0
-    return {"value": f.size * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"3d7pt fp64 {L_3D}^3 for {steps} steps (of {STEPS_3D}), single-threaded C"}
+    single = f.size * steps / dt / 1e9
+    oracle.stencil_run_all_cores(f, offs, w, 1)           # builds the OpenMP library, warms the threads
+    t0 = time.perf_counter()
+    _, threads = oracle.stencil_run_all_cores(f, offs, w, steps)
+    dt = time.perf_counter() - t0
+    return {"value": f.size * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"3d7pt fp64 {L_3D}^3 for {steps} steps (of {STEPS_3D}); the oracle's C built with "
+                      f"OpenMP, planes of a step on {threads} host threads",
+            "single_thread": {"value": single, "cores": 1}}
 
 
 def run_reference(args):
@@ -445,7 +510,8 @@ def main():
     ap.add_argument("--profile", default=None,
                     help="run one small case for ncu and exit: headline, stencil3d-f64, "
                          "stencil3d-f32, stencil3d-bf16, stencil3d-f64-perstep, "
-                         "stencil3d-f32-perstep, stencil384-*, cg-fp64, cg-fp32ir, warmnet-tc, "
+                         "stencil3d-f32-perstep, stencil384-*, stencil192-* (default plan: the resident "
+                         "tile for fp32 / bf16), cg-fp64, cg-fp32ir, warmnet-tc, "
                          "batch64, poisson")
     ap.add_argument("--leg", default=None, choices=["warmstart"],
                     help="run one extra workload and print its JSON (warmstart: the learned "
@@ -453,6 +519,9 @@ def main():
     ap.add_argument("--ws-train", type=int, default=10000, help="warm start: training pairs")
     ap.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
     ap.add_argument("--ws-pool", type=int, default=4, help="warm start: network grid coarsening factor")
+    ap.add_argument("--ws-train-default", type=int, default=2048,
+                    help="warm start inside the default run: training pairs (bounded so the run ends in minutes)")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start leg of the default run")
     args = ap.parse_args()
     if args.leg == "warmstart":
         import torch
@@ -525,7 +594,9 @@ def main():
         sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
     except Exception:
         sm_mhz = 2070.0
-    fp64_peak = fp64_peak_tflops(info["sm_count"], sm_mhz)
+    fp64_derived = fp64_peak_tflops(info["sm_count"], sm_mhz)
+    # measured FP64 pipe throughput (independent FMA chains on every SM), best of 3
+    fp64_peak = max(ctx.fp64_fma_benchmark(40000) for _ in range(3))
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -550,28 +621,53 @@ def main():
             for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
                 r = stencil2d_leg(api, torch, ctx, 256, 100, var, 5, 2)
                 variants[f"2d5pt_256_f64_{vname}"] = {
-                    "gcells": 256 * 256 * 100 / (min(r) * 1e-3) / 1e9, "ms": min(r),
-                    "us_per_step": min(r) * 1e3 / 100}
-            for L, dt in ((192, "f64"), (192, "f32"), (192, "bf16"), (384, "f32"), (384, "bf16")):
-                for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
-                    r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, var, 2, 1)
-                    c = float(L ** 3) * STEPS_3D
-                    d = r["desc"]
-                    ms = min(r["ms"])
-                    variants[f"3d7pt_{L}_{dt}_{vname}"] = {
-                        "gcells": c / (ms * 1e-3) / 1e9, "ms": ms,
-                        "algorithmic_gbs": d["algorithmic_bytes"] / (ms * 1e-3) / 1e9,
-                        "cached_fraction": d["cached_cells"] / max(d["cells"], 1), "plan": r["plan"]}
+                    "gcells": 256 * 256 * 100 / (min(r["ms"]) * 1e-3) / 1e9, "ms": min(r["ms"]),
+                    "us_per_step": min(r["ms"]) * 1e3 / 100, "kernel": r["kernel"], "plan": r["plan"]}
+            # 3d7pt at 192^3 (fits on chip in fp32 / bf16) and 384^3, every storage type; the
+            # fp32 / bf16 results are compared with the fp64 persistent result of the same field
+            # (itself within 1e-12 of the fp64 oracle in the parity tests)
+            for L in (192, 384):
+                ref = None
+                for dt in ("f64", "f32", "bf16"):
+                    if L == 384 and dt == "f64":
+                        r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, api.PERSISTENT, 1, 0, keep_result=True)
+                        ref = r["result"]
+                        continue
+                    for var, vname in ((api.PERSISTENT, "persistent"), (api.PER_STEP, "per_step")):
+                        r = stencil_leg(api, torch, ctx, L, STEPS_3D, dt, var, 2, 1,
+                                        keep_result=(var == api.PERSISTENT))
+                        c = float(L ** 3) * STEPS_3D
+                        d = r["desc"]
+                        ms = min(r["ms"])
+                        v = {"gcells": c / (ms * 1e-3) / 1e9, "ms": ms,
+                             "algorithmic_gbs": d["algorithmic_bytes"] / (ms * 1e-3) / 1e9,
+                             "cached_fraction": d["cached_cells"] / max(d["cells"], 1), "kernel": kernel_name(d),
+                             "threads": d["threads_per_block"], "plan": r["plan"]}
+                        if var == api.PERSISTENT:
+                            if dt == "f64":
+                                ref = r["result"]
+                            elif ref is not None:
+                                v["err_vs_fp64"] = field_error(torch, r["result"], ref)
+                        variants[f"3d7pt_{L}_{dt}_{vname}"] = v
+                        r["result"] = None
+                del ref
+                torch.cuda.empty_cache()
         except Exception as e:
             variants["stencil_error"] = str(e)
         try:
-            variants["cg"] = cg_leg(api, torch, ctx, 2)
+            variants["cg"] = cg_leg(api, torch, ctx, 10)
         except Exception as e:
             variants["cg"] = {"error": str(e)}
         try:
             variants["batch64"] = batch_leg(api, torch, ctx, 2)
         except Exception as e:
             variants["batch64"] = {"error": str(e)}
+        if not args.no_warmstart:
+            try:
+                variants["warmstart"] = warmstart_leg(api, torch, ctx, ntrain=args.ws_train_default,
+                                                      label_rtol=1e-5, pool=args.ws_pool, reps=4)
+            except Exception as e:
+                variants["warmstart"] = {"error": str(e)}
         try:
             variants["grid_barrier_us"] = {str(b): ctx.barrier_benchmark(b, 512, 2000)
                                            for b in (info["sm_count"] // 4, info["sm_count"], 2 * info["sm_count"])}
@@ -601,15 +697,15 @@ def main():
                                                        "tiles_y", "tiles_z", "reg_cache_planes",
                                                        "smem_cache_planes", "cached_cells",
                                                        "halo_cells_per_step")},
-                                "planes_per_barrier": tuned["planes_per_barrier"], "autotuned": True}},
+                                "kernel": kernel_name(desc), "planes_per_sync": desc["planes_per_sync"],
+                                "autotuned": True}},
             "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": tflops / fp64_peak, "traffic": traffic,
-                         "peak_kind": "derived: 152 SMs x 2 fp64 FMA/clk x 2 FLOP x max SM clock "
-                                      f"{sm_mhz:.0f} MHz",
-                         "kernel": "perks_stencil_vec_kernel<double, 3d7pt, NT=512, V=2, ZR=%d, D=8, %s, P=%d>"
-                                   % (8 if tuned["reg_cache"] else 0,
-                                      "cache-free body" if not tuned["reg_cache"] and tuned["smem_cache_planes"] == 0
-                                      else "cached body", tuned["planes_per_barrier"]),
+                         "peak_kind": "measured: fp64 FMA throughput of this GPU (perks_fp64_fma_benchmark, "
+                                      "8 independent chains per thread, 4 x 256 threads per SM, best of 3)",
+                         "derived_peak": {"value": fp64_derived, "how": f"{info['sm_count']} SMs x 2 fp64 FMA/clk "
+                                                                       f"x 2 FLOP x {sm_mhz:.0f} MHz"},
+                         "kernel": kernel_signature(desc, tuned),
                          "flop_per_cell_update": flop_per_cell,
                          "algorithmic_bytes_per_launch": desc["algorithmic_bytes"],
                          "mean_launch_ms": mean_launch_ms,
@@ -656,11 +752,11 @@ def profile_case(name):
             print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d, "tuned": tuned}))
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-    elif name.startswith("stencil3d") or name.startswith("stencil384"):
+    elif name.startswith("stencil3d") or name.startswith("stencil384") or name.startswith("stencil192"):
         dt = "f64" if "f64" in name else ("bf16" if "bf16" in name else "f32")
         variant = api.PER_STEP if name.endswith("perstep") else api.PERSISTENT
-        L = 384 if name.startswith("stencil384") else 256
-        steps = 4 if variant == api.PER_STEP else (8 if L == 384 else 20)
+        L = 384 if name.startswith("stencil384") else (192 if name.startswith("stencil192") else 256)
+        steps = 4 if variant == api.PER_STEP else (8 if L == 384 else (100 if L == 192 else 20))
         shape = (L, L, L)
         f = torch.from_numpy(inputs.stencil_field(shape, 1)).to(
             {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]).cuda()
@@ -740,6 +836,20 @@ def fp64_peak_tflops(sm_count, sm_mhz):
     """GB300's FP64 pipe: 2 fused multiply-adds per clock per SM (1.25 TFLOP/s
     nominal at 2.07 GHz on 152 SMs)."""
     return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_signature(desc, tuned):
+    """The dominant kernel, named from the plan the run actually used."""
+    if desc.get("kernel") == 1:
+        return ("perks_stencil_tile_kernel<double, 3d7pt, NT=%d, V=2, M=%d> (resident tile), tiles %dx%dx%d"
+                % (desc["threads_per_block"], desc["planes_per_sync"], desc["tiles_x"], desc["tiles_y"],
+                   desc["tiles_z"]))
+    body = ("cache-free body" if desc["reg_cache_planes"] == 0 and desc["smem_cache_planes"] == 0
+            else "cached body (%d register + %d shared-memory planes)" % (desc["reg_cache_planes"],
+                                                                          desc["smem_cache_planes"]))
+    return ("perks_stencil_vec_kernel<double, 3d7pt, NT=%d, V=2, ZR=%d, D=%d, P=%d> (plane streaming, %s), "
+            "tiles %dx%dx%d" % (desc["threads_per_block"], desc["reg_cache_planes"], desc["prefetch_planes"],
+                                desc["planes_per_sync"], body, desc["tiles_x"], desc["tiles_y"], desc["tiles_z"]))
 
 
 def desc_signature(desc):

@@ -138,7 +138,9 @@ typedef struct {
 typedef struct {
     int32_t tiles_x, tiles_y, tiles_z;
     int32_t smem_cache_planes;          /* -1: as many as fit; >= 0: at most this many */
-    int32_t reg_cache;                  /* 0: no register cache; 1: the compiled register depth */
+    int32_t reg_cache;                  /* plane streaming: 0 no register cache, 1 the compiled
+                                           register depth; resident tile: rows per thread
+                                           (1 or 2, 0 = automatic) */
     int32_t reserved[4];                /* reserved[0] = 1: one-cell-per-thread kernel instead of
                                            the 16-byte-vector kernel; reserved[1] = planes per
                                            block barrier of the vector kernel (2 or 4, 0 =
@@ -146,8 +148,11 @@ typedef struct {
                                            (PERKS_KERNEL_AUTO / _RESIDENT / _STREAMING; AUTO in a
                                            plan means STREAMING, AUTO with no plan picks the
                                            resident tile when every tile fits in shared memory);
-                                           reserved[3] = threads per block of the resident
-                                           tile kernel (256, 512 or 1024; 0 = automatic) */
+                                           reserved[3] = threads per block (0 = automatic):
+                                           256 or 512 for the resident tile kernel; 256 picks the
+                                           plane-streaming kernel's two-blocks-per-SM
+                                           instantiations where they exist (fp64 3d7pt,
+                                           cache-free body) */
 } perks_stencil_plan;
 
 /* What a run did; filled by perks_stencil_run when asked. */
@@ -156,7 +161,7 @@ typedef struct {
     int32_t variant;                    /* PERKS_PERSISTENT or PERKS_PER_STEP */
     int32_t grid_blocks, threads_per_block;
     int32_t tiles_x, tiles_y, tiles_z;  /* internal orientation: 2-D y maps to z */
-    int32_t reg_cache_planes, smem_cache_planes;
+    int32_t reg_cache_planes, smem_cache_planes;  /* resident tile: rows per thread, planes per tile */
     int32_t prefetch_planes;
     int64_t smem_bytes_per_block;
     int64_t cells;                      /* interior cells */
@@ -199,7 +204,10 @@ perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t 
                                      int32_t *grid_blocks, int32_t *steps);
 
 /* Autotuner (not in the paper): times candidate plans for `variant` on the
- * stencil's current field for `probe_steps` (>= 2) steps each -- the model's
+ * stencil's current field -- each as the difference between runs of
+ * `probe_steps` (>= 2) and 3 `probe_steps` steps, so that the per-run launch,
+ * prologue and epilogue cancel -- the resident-tile kernel with 256 and 512
+ * threads and 1 and 2 rows per thread where the domain fits, and the model's
  * own tiling and up to six tilings ranked by tz * (1 + halo fraction), each
  * with registers + shared memory, shared memory only or no cache, and with 2
  * or 4 planes per block barrier -- restores the field, installs the fastest plan (as

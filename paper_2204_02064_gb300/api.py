@@ -84,8 +84,7 @@ class BatchStats(ctypes.Structure):
                 ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
                 ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
                 ("granularity", ctypes.c_double), ("predicted_ms_per_step", ctypes.c_double),
-                ("algorithmic_bytes", ctypes.c_double), ("kernel", ctypes.c_int32),
-                ("planes_per_sync", ctypes.c_int32)]
+                ("algorithmic_bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -349,18 +348,19 @@ class Stencil:
 
     def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1,
                  scalar: bool = False, planes_per_barrier: int = 0, kernel: int = KERNEL_AUTO,
-                 threads: int = 0):
+                 threads: int = 0, rows: int = 0):
         """Plan override; ``scalar`` selects the one-cell-per-thread kernel
         instead of the 16-byte-vector kernel; ``planes_per_barrier`` (2 or 4,
         0 = automatic) picks how many planes the vector kernel computes
         between two block barriers; ``kernel`` = KERNEL_RESIDENT selects the
-        resident-tile kernel (``tiles`` and ``threads`` 256/512/1024 apply to
+        resident-tile kernel (``tiles`` and ``threads`` 256/512 apply to
         it, 0 = automatic), KERNEL_STREAMING / KERNEL_AUTO the plane-streaming
-        kernel."""
+        kernel; ``rows`` (1 or 2, 0 = automatic) is the resident kernel's
+        rows per thread."""
         p = StencilPlan()
         p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
         p.smem_cache_planes = int(smem_cache_planes)
-        p.reg_cache = int(reg_cache)
+        p.reg_cache = int(rows) if kernel == KERNEL_RESIDENT else int(reg_cache)
         p.reserved[0] = 1 if scalar else 0
         p.reserved[1] = int(planes_per_barrier)
         p.reserved[2] = int(kernel)
@@ -377,6 +377,7 @@ class Stencil:
         return {"tiles": (p.tiles_x, p.tiles_y, p.tiles_z), "reg_cache": p.reg_cache,
                 "smem_cache_planes": p.smem_cache_planes, "planes_per_barrier": p.reserved[1],
                 "kernel": KERNEL_NAMES.get(p.reserved[2], "streaming"), "threads": p.reserved[3],
+                "rows": p.reg_cache if p.reserved[2] == KERNEL_RESIDENT else 0,
                 "ms_per_step": ms.value}
 
     def set_trace(self, steps: int):

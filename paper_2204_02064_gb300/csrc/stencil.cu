@@ -135,11 +135,12 @@ constexpr int kDefaultPlanesPerBarrier = 2;
 // vectors (unless the plan asks for the scalar kernel), the scalar one
 // otherwise; with or without the register cache as requested.
 KernelEntry *find_kernel(int dtype, int shape, bool want_reg, bool per_step, int X, bool allow_vec,
-                         int want_p = 0) {
+                         int want_p = 0, int want_nt = 0) {
     KernelEntry *best = nullptr;
     const int pref_p = want_p > 0 ? want_p : kDefaultPlanesPerBarrier;
     for (KernelEntry &e : registry()) {
         if (e.dtype != dtype || e.shape != shape || e.per_step != per_step) continue;
+        if (want_nt > 0 && e.nt != want_nt) continue;
         if (e.v > 1 && (!allow_vec || X % e.v != 0)) continue;
         if (want_p > 0 && e.v > 1 && e.p != want_p) continue;
         auto score = [&](const KernelEntry &k) {
@@ -164,7 +165,7 @@ struct Plan {
     // tx x tymax x tzmax cells at most
     bool resident = false;
     TileKernelEntry *tk = nullptr;
-    int tx = 0, PP = 0, XGS = 0, groups = 0, chunks = 0;
+    int tx = 0, PP = 0, XGS = 0, groups = 0, chunks = 0, per_plane = 0;
     long long FS = 0;
 };
 
@@ -238,6 +239,7 @@ perks_status make_tile_plan(perks_stencil *st, Plan &pl) {
         return fail(ctx, PERKS_ERR_UNSUPPORTED, "resident-tile kernel: compiled for the 2d5pt and 3d7pt stencils only");
     const bool fixed = st->has_plan && st->plan.reserved[2] == PERKS_KERNEL_RESIDENT;
     const int want_nt = fixed ? st->plan.reserved[3] : 0;
+    const int want_r = fixed ? st->plan.reg_cache : 0;  // resident plans: rows per thread (0 = any)
     const int fx = fixed ? st->plan.tiles_x : 0, fy = fixed ? st->plan.tiles_y : 0, fz = fixed ? st->plan.tiles_z : 0;
     const int GY = shape_by_id(st->shape_id).ndim == 3 ? 1 : 0;
     const int X = st->X, Y = st->Y, Z = st->Z, es = st->es;
@@ -247,7 +249,7 @@ perks_status make_tile_plan(perks_stencil *st, Plan &pl) {
     long long best_smem = 0;
     for (TileKernelEntry &e : tile_registry()) {
         if (e.dtype != st->desc.dtype || e.shape != st->shape_id) continue;
-        if (want_nt > 0 && e.nt != want_nt) continue;
+        if ((want_nt > 0 && e.nt != want_nt) || (want_r > 0 && e.r != want_r)) continue;
         const int V = e.v;
         if (X % V != 0) continue;
         int budget = 0;
@@ -262,7 +264,7 @@ perks_status make_tile_plan(perks_stencil *st, Plan &pl) {
                 if (fy > 0 && nty != fy) continue;
                 const int tymax = ceil_div(Y, nty);
                 if (fy == 0 && nty > 1 && tymax == ceil_div(Y, nty - 1)) continue;  // same tiles, more of them
-                const int P = nvx * tymax;
+                const int P = nvx * ceil_div(tymax, e.r);
                 if (P > e.nt) continue;
                 const int G = e.nt / P;
                 const int ntz = fz > 0 ? fz : std::min(Z, maxG / (ntx * nty));
@@ -280,7 +282,7 @@ perks_status make_tile_plan(perks_stencil *st, Plan &pl) {
                     bp.tk = &e;
                     bp.ntx = ntx; bp.nty = nty; bp.ntz = ntz;
                     bp.tx = tx; bp.txmax = tx; bp.tymax = tymax; bp.tzmax = tzmax;
-                    bp.PP = PP; bp.XGS = XGS; bp.groups = G; bp.chunks = C;
+                    bp.PP = PP; bp.XGS = XGS; bp.groups = G; bp.chunks = C; bp.per_plane = P;
                     best_smem = smem;
                 }
             }
@@ -335,11 +337,12 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
                     "(2d5pt, 2ds9pt, 2d9pt, 2d25pt, 2d13pt, 2d17pt, 3d7pt, 3d13pt, 3d27pt, poisson)");
     const ShapeInfo &sh = shape_by_id(st->shape_id);
     bool want_reg = true, allow_vec = true;
-    int want_p = 0;
+    int want_p = 0, want_nt = 0;
     if (st->has_plan) {
         want_reg = st->plan.reg_cache != 0;
         allow_vec = st->plan.reserved[0] == 0;  // reserved[0] = 1 forces the scalar kernel
         want_p = st->plan.reserved[1];          // planes per barrier (0 = automatic)
+        want_nt = per_step ? 0 : st->plan.reserved[3];  // threads per block (0 = automatic)
     }
     // A persistent plan that caches nothing runs the cache-free kernel body
     // (the per-step one) for all steps in one cooperative launch, with the
@@ -347,13 +350,17 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     // per plane.
     const bool body_per_step = per_step || (st->has_plan && st->plan.reg_cache == 0 &&
                                             st->plan.smem_cache_planes == 0 && allow_vec);
-    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, want_p);
+    KernelEntry *kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, want_p,
+                                  want_nt);
     if (!kp && want_p > 0)
-        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, 0);
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, body_per_step, st->X, allow_vec, 0, want_nt);
     if (!kp && body_per_step && !per_step)  // no vectorised cache-free body for this extent
-        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, false, st->X, allow_vec, want_p);
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, false, st->X, allow_vec, want_p, want_nt);
     if (!kp && !per_step)  // shapes compiled with the cache-free body only (radius 3, 4)
-        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, true, st->X, allow_vec, 0);
+        kp = find_kernel(st->desc.dtype, st->shape_id, want_reg, true, st->X, allow_vec, 0, want_nt);
+    if (!kp && want_nt > 0)
+        return fail(ctx, PERKS_ERR_UNSUPPORTED, "no plane-streaming kernel with %d threads for this dtype/shape",
+                    want_nt);
     per_step = per_step || (kp && kp->per_step);
     if (!kp)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
@@ -365,6 +372,10 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
         perks_status rc = smem_optin(ctx, (const void *)k.fn, &smem_budget);
         if (rc) return rc;
     }
+    // the 256-thread cache-free bodies run two blocks per SM: each block's ring
+    // takes at most half of the SM's shared memory
+    if (!per_step && body_per_step && k.nt <= 256)
+        smem_budget = std::min(smem_budget, ctx->smem_per_sm / 2 - 2048);
     const int R = sh.radius;
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
     const int S = k.v > 1 ? 2 * RZ + k.p + k.d : 2 * RZ + 1 + k.d;  // ring slots (vector kernel: P planes per barrier)
@@ -495,7 +506,7 @@ void fill_stats(const perks_stencil *st, const Plan *pl, long long steps, int va
         o->grid_blocks = pl->blocks;
         o->threads_per_block = pl->tk->nt;
         o->tiles_x = pl->ntx; o->tiles_y = pl->nty; o->tiles_z = pl->ntz;
-        o->reg_cache_planes = 0;
+        o->reg_cache_planes = pl->tk->r;  // rows per thread (their plane window lives in registers)
         o->smem_cache_planes = pl->tzmax;
         o->prefetch_planes = 0;
         o->planes_per_sync = pl->tk->m;
@@ -557,7 +568,9 @@ perks_status run_resident(perks_stencil *st, long long steps, cudaStream_t s, co
     a.ntx = pl.ntx; a.nty = pl.nty; a.ntz = pl.ntz;
     a.tx = pl.tx; a.tymax = pl.tymax; a.tzmax = pl.tzmax;
     a.PP = pl.PP; a.XGS = pl.XGS; a.FS = pl.FS;
-    a.groups = pl.groups; a.chunks = pl.chunks;
+    a.groups = pl.groups; a.chunks = pl.chunks; a.per_plane = pl.per_plane;
+    a.lognv = 0;
+    while ((pl.tx / pl.tk->v) >> a.lognv > 1) ++a.lognv;
     a.steps = steps;
     a.boundary = st->desc.boundary;
     a.boundary_f = (float)st->desc.boundary;
@@ -1003,11 +1016,12 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
     if (rc) { st->has_plan = had_plan; st->plan = saved_plan; return rc; }
     // resident-tile candidates first (their tiling from the planner), one per thread count
     if (!per_step && !st->no_resident)
-        for (int nt : {256, 512, 1024}) {
+        for (int cand = 0; cand < 4; ++cand) {
             perks_stencil_plan p{};
             p.smem_cache_planes = -1;
+            p.reg_cache = 1 + (cand & 1);  // rows per thread
             p.reserved[2] = PERKS_KERNEL_RESIDENT;
-            p.reserved[3] = nt;
+            p.reserved[3] = cand < 2 ? 256 : 512;
             st->plan = p;
             st->has_plan = true;
             Plan probe;
@@ -1016,6 +1030,27 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
                 p.tiles_x = probe.ntx; p.tiles_y = probe.nty; p.tiles_z = probe.ntz;
                 plans.push_back(p);
             }
+            ctx->last_error = saved_msg;
+        }
+    // plane-streaming kernels compiled with 256 threads (two blocks per SM): the model's tiling
+    if (!per_step)
+        for (int P : {2, 4}) {
+            perks_stencil_plan p{};
+            p.smem_cache_planes = 0;
+            p.reg_cache = 0;
+            p.reserved[1] = P;
+            p.reserved[3] = 256;
+            st->plan = p;
+            st->has_plan = true;
+            Plan probe;
+            const std::string saved_msg = ctx->last_error;
+            const bool had = st->no_resident;
+            st->no_resident = true;
+            if (make_plan(st, probe, false) == PERKS_OK && probe.k && probe.k->nt == 256) {
+                p.tiles_x = probe.ntx; p.tiles_y = probe.nty; p.tiles_z = probe.ntz;
+                plans.push_back(p);
+            }
+            st->no_resident = had;
             ctx->last_error = saved_msg;
         }
     st->has_plan = false;
@@ -1049,20 +1084,30 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
         Plan probe;
         if (make_plan(st, probe, per_step) != PERKS_OK) continue;  // plan not hostable
         if (probe.ntx != plans[i].tiles_x || probe.nty != plans[i].tiles_y || probe.ntz != plans[i].tiles_z) continue;
-        ce = cudaMemcpyAsync(st->field[st->cur], saved, bytes, cudaMemcpyDeviceToDevice, s);
-        if (ce != cudaSuccess) break;
-        ce = cudaEventRecord(e0, s);
-        const perks_status r = perks_stencil_run(st, steps, variant, stream, nullptr);
+        // time runs of `steps` and 3 `steps` steps: their difference is the cost of
+        // 2 `steps` steps without the launch, prologue and epilogue of a run
+        // (after one untimed run that allocates the plan's buffers)
+        float ms_run[3] = {0.f, 0.f, 0.f};
+        perks_status r = PERKS_OK;
+        for (int rep = 0; rep < 3 && ce == cudaSuccess && r == PERKS_OK; ++rep) {
+            ce = cudaMemcpyAsync(st->field[st->cur], saved, bytes, cudaMemcpyDeviceToDevice, s);
+            if (ce != cudaSuccess) break;
+            ce = cudaEventRecord(e0, s);
+            r = perks_stencil_run(st, rep < 2 ? steps : 3 * steps, variant, stream, nullptr);
+            if (r != PERKS_OK) break;
+            ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) cudaEventElapsedTime(&ms_run[rep], e0, e1);
+        }
+        ms_run[0] = ms_run[1];
+        ms_run[1] = ms_run[2];
         if (r == PERKS_ERR_LAUNCH_TOO_LARGE || r == PERKS_ERR_UNSUPPORTED) continue;
         if (r != PERKS_OK) { out = r; break; }
-        ce = cudaEventRecord(e1, s);
-        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         if (ce != cudaSuccess) break;
         const perks_status dev = read_dev_error(st, s);
         if (dev != PERKS_OK) { out = dev; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / (double)steps;
+        double per = (ms_run[1] - ms_run[0]) / (2.0 * (double)steps);
+        if (!(per > 0.0)) per = ms_run[1] / (3.0 * (double)steps);
         if (per < best_ms) { best_ms = per; best = plans[i]; }
     }
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(st->field[st->cur], saved, bytes, cudaMemcpyDeviceToDevice, s);

@@ -611,8 +611,8 @@ __device__ __forceinline__ void vec_prologue(const PersistentArgs &a, const VecP
     }
 }
 
-template <typename T, class SH, int NT, int V, int ZR, int D, bool PER_STEP, int P>
-__global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_constant__ PersistentArgs a) {
+template <typename T, class SH, int NT, int V, int ZR, int D, bool PER_STEP, int P, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) perks_stencil_vec_kernel(const __grid_constant__ PersistentArgs a) {
     using VT = VecOf<T, V>;
     using PT = PairOf<T>;
     constexpr int RZ = SH::RZ;
@@ -645,14 +645,15 @@ __global__ void __launch_bounds__(NT, 1) perks_stencil_vec_kernel(const __grid_c
     cp_async_wait_all();
 }
 
-// Registry entry of one instantiation of the vectorised kernel.
-template <typename T, class SH, int NT, int V, int ZR, int D, bool PS, int P = 2>
+// Registry entry of one instantiation of the vectorised kernel (MINB: blocks
+// per SM the register allocation must allow).
+template <typename T, class SH, int NT, int V, int ZR, int D, bool PS, int P = 2, int MINB = 1>
 KernelEntry vec_entry(int dtype, int shape) {
     KernelEntry e;
     e.dtype = dtype;
     e.shape = shape;
     e.per_step = PS;
-    e.fn = perks_stencil_vec_kernel<T, SH, NT, V, ZR, D, PS, P>;
+    e.fn = perks_stencil_vec_kernel<T, SH, NT, V, ZR, D, PS, P, MINB>;
     e.nt = NT;
     e.zr = ZR;
     e.d = D;

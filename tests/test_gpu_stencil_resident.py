@@ -69,16 +69,19 @@ def _check(oracle, name, src, out, steps, dtype, boundary=0.0):
 
 CASES = [
     # (name, grid shape (C order), steps, plan)
-    ("3d7pt", (48, 32, 64), 9, dict(threads=1024)),
-    ("3d7pt", (48, 32, 64), 10, dict(threads=512)),
-    ("3d7pt", (37, 29, 64), 7, dict(threads=1024)),                      # ragged y and z splits
-    ("3d7pt", (37, 29, 64), 8, dict(threads=512, tiles=(2, 3, 5))),
-    ("3d7pt", (61, 5, 32), 6, dict(threads=1024, tiles=(1, 5, 2))),      # one row per tile
-    ("3d7pt", (13, 24, 32), 5, dict(threads=512, tiles=(2, 2, 13))),     # one plane per tile
-    ("3d7pt", (7, 40, 16), 4, dict(threads=1024, tiles=(1, 1, 1))),      # one tile: no halo exchange
-    ("2d5pt", (256, 256), 100, dict(threads=256)),
-    ("2d5pt", (131, 128), 17, dict(threads=1024)),
-    ("2d5pt", (97, 64), 11, dict(threads=256, tiles=(2, 1, 7))),
+    ("3d7pt", (48, 32, 64), 9, dict(threads=512, rows=1)),
+    ("3d7pt", (48, 32, 64), 10, dict(threads=256, rows=2)),
+    ("3d7pt", (37, 29, 64), 7, dict(threads=512, rows=1)),               # ragged y and z splits
+    ("3d7pt", (37, 29, 64), 8, dict(threads=256, rows=2, tiles=(2, 3, 5))),   # odd rows: a half row group
+    ("3d7pt", (61, 5, 32), 6, dict(threads=512, rows=1, tiles=(1, 5, 2))),    # one row per tile
+    ("3d7pt", (61, 5, 32), 6, dict(threads=256, rows=2, tiles=(1, 5, 2))),    # one row: a row group half outside
+    ("3d7pt", (13, 24, 32), 5, dict(threads=512, rows=1, tiles=(2, 2, 13))),  # one plane per tile
+    ("3d7pt", (20, 12, 32), 5, dict(threads=512, rows=1, tiles=(4, 3, 2))),   # 8-cell rows: bf16 lanes own W and E
+    ("3d7pt", (20, 3, 32), 5, dict(threads=256, rows=2, tiles=(4, 3, 2))),    # one-row tiles own both y-faces
+    ("3d7pt", (7, 40, 16), 4, dict(threads=256, rows=2, tiles=(1, 1, 1))),    # one tile: no halo exchange
+    ("2d5pt", (256, 256), 100, dict(threads=256, rows=1)),
+    ("2d5pt", (131, 128), 17, dict(threads=512, rows=1)),
+    ("2d5pt", (97, 64), 11, dict(threads=256, rows=1, tiles=(2, 1, 7))),
 ]
 
 
@@ -91,23 +94,25 @@ def test_resident_matches_oracle(ctx, oracle, name, shape, steps, plan, dtype):
     if "tiles" in plan:
         assert (stats["tiles_x"], stats["tiles_y"], stats["tiles_z"]) == tuple(plan["tiles"])
     assert stats["threads_per_block"] == plan["threads"]
+    assert stats["reg_cache_planes"] == plan["rows"]
     _check(oracle, name, src, out, steps, dtype)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("steps", [1, 2, 3])
-def test_resident_few_steps_and_buffer_parity(ctx, oracle, dtype, steps):
+@pytest.mark.parametrize("rows", [1, 2])
+def test_resident_few_steps_and_buffer_parity(ctx, oracle, dtype, steps, rows):
     """Odd step counts leave the result in the other ping-pong buffer, even
     ones in the buffer that was read (written only after every block read)."""
     f = inputs.stencil_field((24, 40, 32), 43)
-    src, out, _, _ = _run(ctx, "3d7pt", f, steps, dtype, plan=dict(threads=512))
+    src, out, _, _ = _run(ctx, "3d7pt", f, steps, dtype, plan=dict(threads=512 if rows == 1 else 256, rows=rows))
     _check(oracle, "3d7pt", src, out, steps, dtype)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "bf16"])
 def test_resident_nonzero_boundary(ctx, oracle, dtype):
     f = inputs.stencil_field((21, 19, 32), 44)
-    src, out, _, _ = _run(ctx, "3d7pt", f, 13, dtype, plan=dict(threads=1024), boundary=0.625)
+    src, out, _, _ = _run(ctx, "3d7pt", f, 13, dtype, plan=dict(threads=256, rows=2), boundary=0.625)
     _check(oracle, "3d7pt", src, out, 13, dtype, boundary=0.625)
 
 
