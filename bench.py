@@ -766,6 +766,9 @@ def profile_case(name):
         if plan:
             tx, ty, tz, reg, zs, P = (int(v) for v in plan.split(","))
             st.set_plan(tiles=(tx, ty, tz), reg_cache=reg, smem_cache_planes=zs, planes_per_barrier=P)
+        elif name.startswith("stencil192"):
+            st.set_field(f)
+            print(json.dumps({"tuned": st.autotune(variant, probe_steps=10)}))  # the bench's own plan
         for _ in range(2):
             st.set_field(f)
             d = st.run(steps, variant, stats=True)
