@@ -769,9 +769,14 @@ def profile_case(name):
         elif name.startswith("stencil192"):
             st.set_field(f)
             print(json.dumps({"tuned": st.autotune(variant, probe_steps=10)}))  # the bench's own plan
-        for _ in range(2):
-            st.set_field(f)
-            d = st.run(steps, variant, stats=True)
+        st.set_field(f)
+        st.run(steps, variant, stats=True)            # warm-up launch
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("capture")        # ncu --nvtx --nvtx-include capture/ selects this launch
+        st.set_field(f)
+        d = st.run(steps, variant, stats=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"case": name, "L": L, "steps": steps, "plan": d}))
     elif name.startswith("cg"):
         n = 1 << 20

@@ -310,9 +310,22 @@ typedef struct {
     int64_t smem_bytes_per_block;
     int64_t cells, cached_cells, halo_cells_per_step;
     double granularity;                 /* target tile cells / (total cells / blocks) */
-    double predicted_ms_per_step;       /* model makespan of the chosen plan */
+    double predicted_ms_per_step;       /* model makespan of the chosen plan (ring kernel) */
     double algorithmic_bytes;           /* S (2 N D_uncache + 2 D_cache) + S N H */
+    int32_t kernel;                     /* PERKS_BATCH_RING or PERKS_BATCH_STRIP */
+    int32_t strip_rows;                 /* strip kernel: output rows per item (0 = automatic) */
 } perks_batch_stats;
+
+/* Kernels of the batched persistent launch.
+ *   PERKS_BATCH_RING: each block walks its tiles (row ranges of a domain)
+ *     through a shared-memory plane ring and caches the rows its shared
+ *     memory has room for between steps (the PERKS cache split);
+ *   PERKS_BATCH_STRIP: each warp streams its items (a 32-vector-wide column
+ *     strip of a domain over a range of rows) through a private ring of rows
+ *     with 2R + 1 rows of the stencil in registers; halo cells come from the
+ *     previous step's field, so no warp waits for another inside a step; no
+ *     cells are cached between steps (fp32 and fp64 storage). */
+enum { PERKS_BATCH_RING = 0, PERKS_BATCH_STRIP = 1 };
 
 /* Creates a batch of `ndom` 2-D domains, descs[i] each (all the same dtype;
  * shapes 2d5pt, 2d9pt, 2d25pt or 2ds9pt in any mix; nx a multiple of 16 bytes
@@ -331,14 +344,21 @@ perks_status perks_batch_get_field(perks_batch *b, int32_t dom, void *dst, int d
  * (baseline).  opt_out as in perks_stencil_run. */
 perks_status perks_batch_run(perks_batch *b, int64_t steps, int32_t variant, perks_stream stream,
                              perks_batch_stats *opt_out);
-/* Autotuner: ranks tile granularities and width caps with the performance
- * model, times the best few for `probe_steps` steps each (0: model only;
+/* Autotuner: ranks the ring kernel's tile granularities and width caps with
+ * the performance model, times the best few and the strip kernel with items
+ * of 32 to 256 rows for `probe_steps` steps each (0: model only;
  * the fields are restored afterwards) and keeps the fastest plan.  Allocates
  * a temporary copy of the fields while probing.  *chosen may be NULL. */
 perks_status perks_batch_autotune(perks_batch *b, int64_t probe_steps, perks_stream stream,
                                   perks_batch_stats *chosen);
-/* Fixes the plan parameters instead (granularity > 0, width_cap >= 0). */
+/* Fixes the plan parameters instead (granularity > 0, width_cap >= 0) and
+ * selects the ring kernel they apply to. */
 perks_status perks_batch_set_plan(perks_batch *b, double granularity, int32_t width_cap);
+/* Selects the kernel (PERKS_BATCH_RING / PERKS_BATCH_STRIP; the strip kernel
+ * is the default where it is compiled) and, for the strip kernel, the output
+ * rows per item (0 = automatic).  The autotuner times both kernels.  Errors:
+ * INVALID_ARG, UNSUPPORTED (no strip kernel for the dtype). */
+perks_status perks_batch_set_kernel(perks_batch *b, int32_t kernel, int32_t strip_rows);
 
 /* ------------------------------------------------------------------------ */
 /* Conjugate gradient: Sec. 2.2.2 (algorithm), Sec. 4.3 (PERKS port)          */

@@ -19,6 +19,7 @@ MAX_POINTS = 125
 F64, F32, BF16 = 0, 1, 2
 PERSISTENT, PER_STEP = 0, 1
 KERNEL_AUTO, KERNEL_RESIDENT, KERNEL_STREAMING, KERNEL_PER_STEP = 0, 1, 2, 3
+BATCH_RING, BATCH_STRIP = 0, 1
 KERNEL_NAMES = {KERNEL_RESIDENT: "resident", KERNEL_STREAMING: "streaming", KERNEL_PER_STEP: "per_step"}
 CG_FP64, CG_FP32_IR, CG_FP64_MULTI = 0, 1, 2
 SPMV_ROWVEC, SPMV_MERGE, SPMV_SEG = 0, 1, 2
@@ -84,7 +85,8 @@ class BatchStats(ctypes.Structure):
                 ("smem_bytes_per_block", ctypes.c_int64), ("cells", ctypes.c_int64),
                 ("cached_cells", ctypes.c_int64), ("halo_cells_per_step", ctypes.c_int64),
                 ("granularity", ctypes.c_double), ("predicted_ms_per_step", ctypes.c_double),
-                ("algorithmic_bytes", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_double), ("kernel", ctypes.c_int32),
+                ("strip_rows", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -129,6 +131,7 @@ def _declare(lib):
         "perks_cg_last_result": ([P, P, ctypes.POINTER(CgStats)], i32),
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_fp64_fma_benchmark": ([P, i32, ctypes.POINTER(f64)], i32),
+        "perks_batch_set_kernel": ([P, i32, i32], i32),
         "perks_op_set_spmv": ([P, i32], i32),
         "perks_op_set_vector_cache": ([P, i32], i32),
         "perks_op_vector_cache_active": ([P], i32),
@@ -585,7 +588,12 @@ class Batch:
         return s.as_dict()
 
     def set_plan(self, granularity: float = 1.0, width_cap: int = 0):
+        """Ring kernel with this tile granularity and width cap."""
         self.ctx.check(self._lib.perks_batch_set_plan(self.handle, float(granularity), int(width_cap)))
+
+    def set_kernel(self, kernel: int, strip_rows: int = 0):
+        """BATCH_RING or BATCH_STRIP (rows per strip item, 0 = automatic)."""
+        self.ctx.check(self._lib.perks_batch_set_kernel(self.handle, int(kernel), int(strip_rows)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -116,6 +116,169 @@ __global__ void __launch_bounds__(kBatchThreads, 1) perks_batch_kernel(const __g
     cp_async_wait_all();
 }
 
+// ------------------------------------------------------------- strip kernel
+//
+// Column-strip streaming: the batch's work is cut into items (domain, strip
+// of 32 vectors = 32 V cells, range of rows) and a static
+// longest-processing-time-first assignment gives every WARP its items.  A
+// warp streams its item's input rows through a private ring of D row slots
+// in shared memory (16-byte cp.async per lane, plus two halo cells on each
+// side from the neighbouring strips), keeps the 2R + 1 rows the stencil
+// reads in registers, and writes each output row with one 16-byte store per
+// lane.  Halo cells come straight from the previous step's field, which
+// nobody writes during the step, so warps never wait for each other inside a
+// step: the only synchronisation is the grid barrier between steps.  Nothing
+// is cached between steps (D_cache = 0): each step reads and writes every
+// cell once, which is the HBM roofline of a domain set larger than the
+// on-chip memory (171 MB of fp32 for the 64-domain workload).
+
+struct StripItem {
+    int dom;
+    int x0;      // first cell of the strip (a multiple of 32 V)
+    int z0, z1;  // output rows [z0, z1)
+};
+
+struct StripArgs {
+    const PersistentArgs *doms;  // per-domain extents, weights, boundary, field[2]
+    const int *dom_shape;
+    const StripItem *items;      // items in warp order
+    const int *warp_first;       // nwarps + 1 offsets into items
+    long long steps;
+    unsigned long long *bar;
+    DevError *err;
+    long long timeout_ns;
+};
+
+constexpr int kStripThreads = 256;
+constexpr int kStripDepth = 8;   // ring rows per warp
+
+template <typename T, int V>
+__host__ __device__ constexpr int strip_row_cells() { return 32 * V + 2 * V; }  // V pad cells on each side
+
+// One item: output rows z0..z1-1 of the strip at x0.
+template <typename T, class SH, int V, int D>
+__device__ __forceinline__ void strip_item(const PersistentArgs &a, const StripItem it, int src, T *ring, int lane) {
+    using A = typename ScalarOps<T>::A;
+    using VT = VecOf<T, V>;
+    constexpr int R = SH::R;
+    constexpr int W = 2 * R + 1;
+    constexpr int ROW = strip_row_cells<T, V>();
+    static_assert(R <= 2 && D > 2 * R, "strip ring depth");
+    const T *in = static_cast<const T *>(a.field[src]);
+    T *out = static_cast<T *>(a.field[src ^ 1]);
+    const int X = a.X, Z = a.Z;
+    const int xl = it.x0 + lane * V;
+    const bool own = xl < X;
+    const T bnd = ScalarOps<T>::bnd(a);
+    A w[SH::NPTS];
+#pragma unroll
+    for (int i = 0; i < SH::NPTS; ++i) w[i] = ScalarOps<T>::w(a, i);
+    const int rfirst = it.z0 - R, rlast = it.z1 - 1 + R;
+
+    // row r into ring slot (r - rfirst) % D; one cp.async group per row
+    auto issue = [&](int r) {
+        T *dst = ring + ((r - rfirst) % D) * ROW;
+        const bool rin = r >= 0 && r < Z && r <= rlast;
+        const long long rb = (long long)r * X;
+        if (rin && own) cp_async<16>(dst + V + lane * V, in + rb + xl);
+        else set_vec<T, V>(dst + V + lane * V, bnd);
+        if (lane == 0) {
+            if (rin && it.x0 >= 2) cp_async<2 * sizeof(T)>(dst + V - 2, in + rb + it.x0 - 2);
+            else { dst[V - 2] = bnd; dst[V - 1] = bnd; }
+        }
+        if (lane == 31) {
+            const int xr = it.x0 + 32 * V;
+            if (rin && xr + 2 <= X) cp_async<2 * sizeof(T)>(dst + V + 32 * V, in + rb + xr);
+            else { dst[V + 32 * V] = bnd; dst[V + 32 * V + 1] = bnd; }
+        }
+        cp_async_commit();
+    };
+    // the lane's cells -2 .. V+1 of row r (from its ring slot), in the accumulator type
+    auto fetch = [&](int r, A (&row)[V + 4]) {
+        cp_async_wait<D - 1>();
+        __syncwarp();
+        const T *p = ring + ((r - rfirst) % D) * ROW + V + lane * V;
+        const VT c = *reinterpret_cast<const VT *>(p);
+        const PairOf<T> l = *reinterpret_cast<const PairOf<T> *>(p - 2);
+        const PairOf<T> h = *reinterpret_cast<const PairOf<T> *>(p + V);
+        row[0] = to_acc(l.v[0]);
+        row[1] = to_acc(l.v[1]);
+#pragma unroll
+        for (int j = 0; j < V; ++j) row[2 + j] = to_acc(c.v[j]);
+        row[V + 2] = to_acc(h.v[0]);
+        row[V + 3] = to_acc(h.v[1]);
+        __syncwarp();  // every lane has read the slot before it is refilled
+        issue(r + D);
+    };
+
+    for (int j = 0; j < D; ++j) issue(rfirst + j);
+    A win[W][V + 4];
+    // the first 2R rows of the window: rows z0-R .. z0+R-1 in slots 0 .. 2R-1
+    static_for<0, 2 * R>([&](auto JI) { fetch(rfirst + decltype(JI)::value, win[decltype(JI)::value]); });
+    // output row z reads window slots (z - rfirst + k) % W, k = 0..2R; the loop
+    // advances W rows per turn so that every slot index is a constant
+    for (int zb = it.z0; zb < it.z1; zb += W) {
+        static_for<0, W>([&](auto PI) {
+            constexpr int p = decltype(PI)::value;
+            const int z = zb + p;
+            if (z < it.z1) {
+                fetch(z + R, win[(p + 2 * R) % W]);
+                VT o;
+                A acc[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] = A(0);
+                static_for<0, SH::NPTS>([&](auto II) {
+                    constexpr int i = decltype(II)::value;
+                    constexpr int slot = (p + R + SH::dz(i)) % W;
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[q] = fma(w[i], win[slot][2 + q + SH::dx(i)], acc[q]);
+                });
+                if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+                    __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+                    for (int q = 0; q < V / 2; ++q) o2[q] = __floats2bfloat162_rn(acc[2 * q], acc[2 * q + 1]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) o.v[q] = from_acc<T>(acc[q]);
+                }
+                if (own) *reinterpret_cast<VT *>(out + (long long)z * X + xl) = o;
+            }
+        });
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kStripThreads, sizeof(T) == 8 ? 1 : 2)
+    perks_batch_strip_kernel(const __grid_constant__ StripArgs b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int D = kStripDepth;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *ring = reinterpret_cast<T *>(smem_raw) + (long long)warp * D * strip_row_cells<T, V>();
+    const int gw = blockIdx.x * (kStripThreads / 32) + warp;
+    const int i0 = b.warp_first[gw], i1 = b.warp_first[gw + 1];
+    unsigned long long epoch = 0;
+    for (long long k = 0; k < b.steps; ++k) {
+        const int src = (int)(k & 1);
+        for (int q = i0; q < i1; ++q) {
+            const StripItem it = b.items[q];
+            const PersistentArgs &a = b.doms[it.dom];
+            switch (b.dom_shape[it.dom]) {
+            case SH_2D5: strip_item<T, S2d5, V, D>(a, it, src, ring, lane); break;
+            case SH_2D9: strip_item<T, S2d9, V, D>(a, it, src, ring, lane); break;
+            case SH_2D25: strip_item<T, S2d25, V, D>(a, it, src, ring, lane); break;
+            default: strip_item<T, S2ds9, V, D>(a, it, src, ring, lane); break;
+            }
+        }
+        if (k + 1 < b.steps) {
+            if (!grid_barrier(b.bar, gridDim.x, epoch, b.err, b.timeout_ns)) return;
+        }
+    }
+}
+
+using StripFn = void (*)(StripArgs);
+
 using BatchFn = void (*)(BatchArgs);
 
 struct BatchKernel {
@@ -131,6 +294,13 @@ std::vector<BatchKernel> &batch_kernels() {
         {PERKS_BF16, 8, 16, perks_batch_kernel<__nv_bfloat16, 8, 16>},
     };
     return k;
+}
+
+// Strip kernels (column-strip streaming), by storage type.
+StripFn strip_kernel(int dtype) {
+    if (dtype == PERKS_F32) return perks_batch_strip_kernel<float, 4>;
+    if (dtype == PERKS_F64) return perks_batch_strip_kernel<double, 2>;
+    return nullptr;
 }
 
 int shape_id_2d(const perks_stencil_desc &d, double *kw) {
@@ -207,6 +377,18 @@ struct perks_batch {
     double predicted_ms_per_step = 0.0;
     std::vector<PersistentArgs> h_doms;
     std::vector<perks_stencil *> per_step;  // baseline objects, one per domain
+    // kernel choice: PERKS_BATCH_RING (tiles of rows through a plane ring) or
+    // PERKS_BATCH_STRIP (column strips streamed by single warps)
+    int kernel = PERKS_BATCH_RING;
+    int strip_rows = 0;            // strip kernel: output rows per item (0 = automatic)
+    StripItem *d_items = nullptr;
+    int *d_warp_first = nullptr;
+    size_t cap_items = 0, cap_warps = 0;
+    int strip_blocks = 0;          // grid of the current strip plan (0: none)
+    int nitems = 0, max_items_per_warp = 0;
+    long long strip_halo = 0, strip_smem = 0;
+    std::vector<PersistentArgs> h_sdoms;
+    PersistentArgs *d_sdoms = nullptr;
 };
 
 namespace {
@@ -399,6 +581,140 @@ perks_status upload_plan(perks_batch *b, const PlanOut &o) {
     return PERKS_OK;
 }
 
+// Strip plan: items of `rows` output rows (0: as many as give every warp
+// about one item's worth of rows), longest-processing-time-first over the
+// warps of a co-resident grid.  Item cost = rows read (its rows plus 2R of
+// halo) x (1 + points / 25): the stream of rows, plus the stencil's FMAs.
+perks_status plan_strips(perks_batch *b, int rows) {
+    perks_context *ctx = b->ctx;
+    StripFn fn = strip_kernel(b->dtype);
+    if (!fn) return fail(ctx, PERKS_ERR_UNSUPPORTED, "batch: no strip kernel for this dtype");
+    const int V = (int)(16 / b->es);
+    const int W = 32 * V;
+    const size_t smem = (size_t)(kStripThreads / 32) * kStripDepth * (32 * V + 2 * V) * b->es;
+    int budget = 0;
+    perks_status rc = smem_optin(ctx, (const void *)fn, &budget);
+    if (rc) return rc;
+    int per_sm = 0;
+    PERKS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kStripThreads, smem));
+    if (per_sm < 1) return fail(ctx, PERKS_ERR_LAUNCH_TOO_LARGE, "batch strip kernel is not resident");
+    const int G = per_sm * ctx->sm_count;
+    const int nwarps = G * (kStripThreads / 32);
+    long long total_rows = 0;
+    for (const auto &d : b->desc) total_rows += (long long)ceil_div((int)d.nx, W) * d.ny;
+    const int target = rows > 0 ? rows : (int)std::min<long long>(1024, std::max<long long>(8, total_rows / nwarps));
+    std::vector<StripItem> items;
+    std::vector<double> cost;
+    long long halo = 0;
+    for (int i = 0; i < b->ndom; ++i) {
+        const int X = (int)b->desc[i].nx, Z = (int)b->desc[i].ny, R = b->desc[i].radius;
+        const int nseg = std::max(1, (int)std::lround((double)Z / target));
+        for (int x0 = 0; x0 < X; x0 += W)
+            for (int sgi = 0; sgi < nseg; ++sgi) {
+                int z0, nz;
+                split_axis(Z, nseg, sgi, z0, nz);
+                items.push_back(StripItem{i, x0, z0, z0 + nz});
+                cost.push_back((double)(nz + 2 * R) * (1.0 + b->desc[i].npts / 25.0));
+                halo += 2LL * R * std::min(W, X - x0) + 4LL * (nz + 2 * R);
+            }
+    }
+    // LPT: the costliest item to the least loaded warp
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::pair<double, int>> heap;  // (load, warp), min-heap
+    heap.reserve(nwarps);
+    for (int w = 0; w < nwarps; ++w) heap.push_back({0.0, w});
+    auto cmp = [](const std::pair<double, int> &x, const std::pair<double, int> &y) { return x.first > y.first; };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    std::vector<std::vector<int>> per_warp(nwarps);
+    for (int q : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto &top = heap.back();
+        per_warp[top.second].push_back(q);
+        top.first += cost[q];
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<StripItem> sorted;
+    std::vector<int> first(nwarps + 1, 0);
+    int maxw = 0;
+    for (int w = 0; w < nwarps; ++w) {
+        first[w] = (int)sorted.size();
+        for (int q : per_warp[w]) sorted.push_back(items[q]);
+        maxw = std::max(maxw, (int)per_warp[w].size());
+    }
+    first[nwarps] = (int)sorted.size();
+    if (sorted.size() > b->cap_items) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        PERKS_CUDA(ctx, cudaMalloc(&b->d_items, sorted.size() * sizeof(StripItem)));
+        b->cap_items = sorted.size();
+    }
+    if ((size_t)nwarps + 1 > b->cap_warps) {
+        if (b->d_warp_first) cudaFree(b->d_warp_first);
+        b->d_warp_first = nullptr;
+        PERKS_CUDA(ctx, cudaMalloc(&b->d_warp_first, (nwarps + 1) * sizeof(int)));
+        b->cap_warps = (size_t)nwarps + 1;
+    }
+    PERKS_CUDA(ctx, cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(StripItem), cudaMemcpyHostToDevice));
+    PERKS_CUDA(ctx, cudaMemcpy(b->d_warp_first, first.data(), (nwarps + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if (!b->d_sdoms) PERKS_CUDA(ctx, cudaMalloc(&b->d_sdoms, b->ndom * sizeof(PersistentArgs)));
+    if (!b->d_shape) PERKS_CUDA(ctx, cudaMalloc(&b->d_shape, b->ndom * sizeof(int)));
+    PERKS_CUDA(ctx, cudaMemcpy(b->d_shape, b->shape.data(), b->ndom * sizeof(int), cudaMemcpyHostToDevice));
+    b->h_sdoms.assign(b->ndom, PersistentArgs{});
+    for (int i = 0; i < b->ndom; ++i) {
+        PersistentArgs &a = b->h_sdoms[i];
+        std::memset(&a, 0, sizeof(a));
+        a.X = (int)b->desc[i].nx; a.Y = 1; a.Z = (int)b->desc[i].ny;
+        a.XY = a.X;
+        a.boundary = b->desc[i].boundary;
+        a.boundary_f = (float)b->desc[i].boundary;
+        for (int j = 0; j < kMaxKernelPoints && j < (int)b->kw[i].size(); ++j) {
+            a.w[j] = b->kw[i][j];
+            a.wf[j] = (float)b->kw[i][j];
+        }
+    }
+    b->strip_blocks = G;
+    b->nitems = (int)sorted.size();
+    b->max_items_per_warp = maxw;
+    b->strip_halo = halo;
+    b->strip_smem = (long long)smem;
+    return PERKS_OK;
+}
+
+perks_status launch_strips(perks_batch *b, long long steps, cudaStream_t s) {
+    perks_context *ctx = b->ctx;
+    if (b->strip_blocks == 0) {
+        perks_status rc = plan_strips(b, b->strip_rows);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < b->ndom; ++i) {
+        PersistentArgs &a = b->h_sdoms[i];
+        a.field[0] = b->field[b->cur[i]][i];
+        a.field[1] = b->field[b->cur[i] ^ 1][i];
+        a.steps = steps;
+    }
+    PERKS_CUDA(ctx, cudaMemcpyAsync(b->d_sdoms, b->h_sdoms.data(), b->ndom * sizeof(PersistentArgs),
+                                    cudaMemcpyHostToDevice, s));
+    PERKS_CUDA(ctx, cudaMemsetAsync(b->bar, 0, sizeof(unsigned long long), s));
+    PERKS_CUDA(ctx, cudaMemsetAsync(b->err, 0, sizeof(DevError), s));
+    StripArgs args;
+    args.doms = b->d_sdoms;
+    args.dom_shape = b->d_shape;
+    args.items = b->d_items;
+    args.warp_first = b->d_warp_first;
+    args.steps = steps;
+    args.bar = b->bar;
+    args.err = b->err;
+    args.timeout_ns = ctx->timeout_ns;
+    void *kargs[] = {&args};
+    PERKS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)strip_kernel(b->dtype), dim3(b->strip_blocks),
+                                                dim3(kStripThreads), kargs, (size_t)b->strip_smem, s));
+    if (steps & 1)
+        for (int i = 0; i < b->ndom; ++i) b->cur[i] ^= 1;
+    return PERKS_OK;
+}
+
 perks_status ensure_plan(perks_batch *b) {
     BatchKernel *k = batch_kernel(b);
     if (!k) return fail(b->ctx, PERKS_ERR_UNSUPPORTED, "batch: no kernel for this dtype");
@@ -506,6 +822,7 @@ extern "C" perks_status perks_batch_create(perks_context *ctx, int32_t ndom, con
         b->shape.push_back(id);
         b->kw.push_back(kw);
     }
+    b->kernel = strip_kernel(dtype) ? PERKS_BATCH_STRIP : PERKS_BATCH_RING;
     for (int p = 0; p < 2; ++p) b->field[p].assign(ndom, nullptr), b->faces[p].assign(ndom, nullptr);
     b->faces_bytes.assign(ndom, 0);
     b->cur.assign(ndom, 0);
@@ -530,7 +847,8 @@ extern "C" perks_status perks_batch_destroy(perks_batch *b) {
         for (void *q : b->field[p]) if (q) cudaFree(q);
         for (void *q : b->faces[p]) if (q) cudaFree(q);
     }
-    void *ptrs[] = {b->bar, b->err, b->d_doms, b->d_shape, b->d_tiles, b->d_block_first, b->d_tile_list};
+    void *ptrs[] = {b->bar, b->err, b->d_doms, b->d_shape, b->d_tiles, b->d_block_first, b->d_tile_list,
+                    b->d_items, b->d_warp_first, b->d_sdoms};
     for (void *q : ptrs) if (q) cudaFree(q);
     for (perks_stencil *st : b->per_step) perks_stencil_destroy(st);
     delete b;
@@ -578,9 +896,20 @@ static void fill_batch_stats(const perks_batch *b, long long steps, perks_batch_
     o->granularity = b->granularity;
     o->width_cap = b->width_cap;
     o->predicted_ms_per_step = b->predicted_ms_per_step;
+    o->kernel = b->kernel;
+    o->strip_rows = b->strip_rows;
+    if (b->kernel == PERKS_BATCH_STRIP) {
+        o->grid_blocks = b->strip_blocks;
+        o->tiles = b->nitems;
+        o->max_tiles_per_block = b->max_items_per_warp;
+        o->smem_bytes_per_block = b->strip_smem;
+        o->cached_cells = 0;
+        o->halo_cells_per_step = b->strip_halo;
+        o->predicted_ms_per_step = 0.0;
+    }
     const double S = b->es;
-    o->algorithmic_bytes = steps > 0 ? S * (2.0 * steps * (double)(cells - b->cached_cells) +
-                                            2.0 * b->cached_cells + (double)steps * b->halo_cells)
+    o->algorithmic_bytes = steps > 0 ? S * (2.0 * steps * (double)(cells - o->cached_cells) +
+                                            2.0 * o->cached_cells + (double)steps * o->halo_cells_per_step)
                                      : 0.0;
 }
 
@@ -593,11 +922,13 @@ extern "C" perks_status perks_batch_run(perks_batch *b, int64_t steps, int32_t v
     perks_status rc = use_device(ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool strip = b->kernel == PERKS_BATCH_STRIP;
     if (steps > 0) {
-        rc = variant == PERKS_PERSISTENT ? launch_batch(b, steps, s) : launch_batch_per_step(b, steps, s);
+        rc = variant == PERKS_PERSISTENT ? (strip ? launch_strips(b, steps, s) : launch_batch(b, steps, s))
+                                         : launch_batch_per_step(b, steps, s);
         if (rc) return rc;
     } else {
-        rc = ensure_plan(b);
+        rc = strip ? (b->strip_blocks ? PERKS_OK : plan_strips(b, b->strip_rows)) : ensure_plan(b);
         if (rc) return rc;
     }
     if (opt_out) {
@@ -636,6 +967,7 @@ extern "C" perks_status perks_batch_autotune(perks_batch *b, int64_t probe_steps
     std::sort(cands.begin(), cands.end(), [](const Cand &x, const Cand &y) { return x.pred < y.pred; });
     // 2. time the best model candidates on the GPU (the field is saved and restored)
     Cand best = cands[0];
+    int best_strip_rows = -1;  // >= 0: the strip kernel with items of that height won
     if (probe_steps > 0) {
         cudaStream_t s = (cudaStream_t)stream;
         std::vector<void *> saved(b->ndom, nullptr);
@@ -665,6 +997,23 @@ extern "C" perks_status perks_batch_autotune(perks_batch *b, int64_t probe_steps
             cudaEventElapsedTime(&ms, e0, e1);
             if (!rc && ms < best_ms) { best_ms = ms; best = cands[c]; }
         }
+        // the strip kernel, with items of several heights
+        if (!rc && strip_kernel(b->dtype)) {
+            for (int rows : {0, 32, 64, 128, 256}) {
+                b->strip_blocks = 0;
+                rc = plan_strips(b, rows);
+                if (rc) break;
+                rc = launch_strips(b, 1, s);  // warm-up
+                cudaEventRecord(e0, s);
+                if (!rc) rc = launch_strips(b, probe_steps, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rc) break;
+                if (ms < best_ms) { best_ms = ms; best_strip_rows = rows; }
+            }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (int i = 0; i < b->ndom; ++i) {
@@ -680,6 +1029,15 @@ extern "C" perks_status perks_batch_autotune(perks_batch *b, int64_t probe_steps
     b->blocks = 0;
     rc = ensure_plan(b);
     if (rc) return rc;
+    b->strip_blocks = 0;
+    if (best_strip_rows >= 0) {
+        b->kernel = PERKS_BATCH_STRIP;
+        b->strip_rows = best_strip_rows;
+        rc = plan_strips(b, best_strip_rows);
+        if (rc) return rc;
+    } else if (probe_steps > 0) {
+        b->kernel = PERKS_BATCH_RING;
+    }
     b->tuned = true;
     if (chosen) fill_batch_stats(b, 0, chosen);
     return PERKS_OK;
@@ -692,5 +1050,18 @@ extern "C" perks_status perks_batch_set_plan(perks_batch *b, double granularity,
     b->granularity = granularity;
     b->width_cap = width_cap;
     b->blocks = 0;
+    b->kernel = PERKS_BATCH_RING;
+    return PERKS_OK;
+}
+
+extern "C" perks_status perks_batch_set_kernel(perks_batch *b, int32_t kernel, int32_t strip_rows) {
+    if (!b) return PERKS_ERR_INVALID_ARG;
+    if ((kernel != PERKS_BATCH_RING && kernel != PERKS_BATCH_STRIP) || strip_rows < 0)
+        return fail(b->ctx, PERKS_ERR_INVALID_ARG, "batch_set_kernel: kernel RING or STRIP, strip_rows >= 0");
+    if (kernel == PERKS_BATCH_STRIP && !strip_kernel(b->dtype))
+        return fail(b->ctx, PERKS_ERR_UNSUPPORTED, "batch_set_kernel: no strip kernel for this dtype");
+    b->kernel = kernel;
+    b->strip_rows = strip_rows;
+    b->strip_blocks = 0;
     return PERKS_OK;
 }

@@ -42,6 +42,9 @@ perks_status smem_optin(perks_context *ctx, const void *fn, int *budget) {
     const bool known = rec && ctx->device < 64 && (rec->devices >> ctx->device & 1ull);
     if (!known) {
         PERKS_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        // every persistent kernel wants the largest shared-memory share of the SM
+        PERKS_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
         if (rec && ctx->device < 64) rec->devices |= 1ull << ctx->device;
     }
     *budget = b;

@@ -374,8 +374,8 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     }
     // the 256-thread cache-free bodies run two blocks per SM: each block's ring
     // takes at most half of the SM's shared memory
-    if (!per_step && body_per_step && k.nt <= 256)
-        smem_budget = std::min(smem_budget, ctx->smem_per_sm / 2 - 2048);
+    if (k.per_step && k.v > 1 && k.nt <= 256 && k.shape == SH_3D7)
+        smem_budget = std::min(smem_budget, ctx->smem_per_sm / 2 - 4096);
     const int R = sh.radius;
     const int RX = R, RY = sh.ndim == 3 ? R : 0, RZ = R;
     const int S = k.v > 1 ? 2 * RZ + k.p + k.d : 2 * RZ + 1 + k.d;  // ring slots (vector kernel: P planes per barrier)
@@ -433,8 +433,9 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     }
     if (bp.ntx == 0)
         return fail(ctx, PERKS_ERR_UNSUPPORTED,
-                    "persistent kernel: no tile decomposition of %dx%dx%d fits %d blocks of %d threads",
-                    X, Y, Z, maxG, k.nt);
+                    "persistent kernel: no tile decomposition of %dx%dx%d fits %d blocks of %d threads "
+                    "(%d per SM with %d bytes of shared memory each)",
+                    X, Y, Z, maxG, k.nt, per_sm, smem_budget);
     bp.k = &k;
     bp.plane = bp.PW * bp.PH;
     bp.ncol = bp.txmax * bp.tymax;

@@ -100,3 +100,48 @@ def test_batch_full_size_workload(ctx, oracle):
         d = doms[i]
         ref = oracle.stencil_run_lowp(srcs[i].astype(np.float32), d["offsets"], d["weights"], 500, "f32")
         assert np.array_equal(outs[i].astype(np.float32), ref)
+
+
+@pytest.mark.parametrize("rows", [0, 1, 3, 7, 64])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_strip_kernel_matches_oracle(ctx, oracle, dtype, rows):
+    """The column-strip kernel (each warp streams 32-vector strips of rows
+    through its own ring): items of 1 row (every row a new pipeline), odd
+    heights (ragged row splits), narrow domains (a strip wider than the
+    domain: idle lanes read the Dirichlet value) and a 2056-wide one (a
+    strip of two vectors after the full ones); fp32 bit for bit against the
+    low-precision oracle, fp64 within 1e-12."""
+    from paper_2204_02064_gb300 import api
+    doms = small_domains()
+    b = api.Batch(ctx, doms, dtype=dtype)
+    b.set_kernel(api.BATCH_STRIP, rows)
+    srcs = []
+    for i, d in enumerate(doms):
+        f = torch.from_numpy(inputs.stencil_field(d["shape"], d["seed"])).to(TT[dtype]).cuda()
+        srcs.append(f)
+        b.set_field(i, f)
+    st = b.run(12, stats=True)
+    assert st["kernel"] == api.BATCH_STRIP and st["strip_rows"] == rows
+    for i, (d, f) in enumerate(zip(doms, srcs)):
+        o = torch.empty_like(f)
+        b.get_field(i, o)
+        torch.cuda.synchronize()
+        if dtype == "f32":
+            ref = oracle.stencil_run_lowp(f.cpu().numpy(), d["offsets"], d["weights"], 12, "f32")
+            assert np.array_equal(o.cpu().numpy(), ref), d["name"]
+        else:
+            ref = oracle.stencil_run(f.cpu().numpy(), d["offsets"], d["weights"], 12)
+            assert rel_err(o.cpu().numpy(), ref) <= 1e-12, d["name"]
+    b.close()
+
+
+def test_batch_strip_equals_ring_bitwise(ctx):
+    """Both persistent batch kernels add the same fp32 FMA chains: identical
+    fields after 21 steps, and the default kernel is the strip kernel."""
+    from paper_2204_02064_gb300 import api
+    doms = small_domains()
+    _, a, sa = _run(ctx, doms, 21, "f32")
+    _, r, sr = _run(ctx, doms, 21, "f32", plan=dict(granularity=1.0, width_cap=0))
+    assert sa["kernel"] == api.BATCH_STRIP and sr["kernel"] == api.BATCH_RING
+    for x, y in zip(a, r):
+        assert np.array_equal(x, y)
