@@ -286,6 +286,34 @@ def cg_leg(api, torch, ctx, K):
                          / (med * 1e-3) / 1e9}
         except Exception as e:  # report, do not hide
             out[name] = {"error": str(e)}
+    # the SpMV alone, against the rate at which this GPU serves random 8-byte
+    # gathers from an L2-resident vector (its ceiling for a matrix whose
+    # columns are scattered uniformly) and against HBM for its bytes
+    try:
+        op.set_spmv(api.SPMV_ROWVEC)
+        xv = torch.rand(n, dtype=torch.float64, device="cuda")
+        yv = torch.empty_like(xv)
+        op.spmv(xv, yv)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            op.spmv(xv, yv)
+        e1.record(stream)
+        e1.synchronize()
+        spmv_ms = e0.elapsed_time(e1) / 20
+        g = ctx.gather_benchmark(20, 2000)
+        g4 = ctx.gather_benchmark(20, 2000, elem_bytes=4)
+        nnz = int(c.shape[0])
+        hbm_bytes = 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+        out["spmv_alone"] = {"ms": spmv_ms, "gathers_per_s": g, "gathers_per_s_4byte": g4,
+                             "gather_bound_ms": nnz / g * 1e3,
+                             "frac_of_gather_bound": nnz / g * 1e3 / spmv_ms,
+                             "hbm_bound_ms": hbm_bytes / (_peaks()[0] * 1e9) * 1e3,
+                             "frac_of_hbm_bound": hbm_bytes / (_peaks()[0] * 1e9) * 1e3 / spmv_ms}
+    except Exception as e:
+        out["spmv_alone"] = {"error": str(e)}
     op.close()
     return out
 
@@ -513,12 +541,15 @@ def main():
                          "stencil3d-f32-perstep, stencil384-*, stencil192-* (default plan: the resident "
                          "tile for fp32 / bf16), cg-fp64, cg-fp32ir, warmnet-tc, "
                          "batch64, poisson")
-    ap.add_argument("--leg", default=None, choices=["warmstart"],
-                    help="run one extra workload and print its JSON (warmstart: the learned "
-                         "warm start for the 512^2 x 256 Poisson problems)")
+    ap.add_argument("--leg", default=None, choices=["warmstart", "cg"],
+                    help="run one workload alone and print its JSON (warmstart: the learned "
+                         "warm start for the 512^2 x 256 Poisson problems; cg: the n = 2^20 CG legs "
+                         "and the SpMV against its gather and HBM bounds)")
     ap.add_argument("--ws-train", type=int, default=10000, help="warm start: training pairs")
     ap.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
-    ap.add_argument("--ws-pool", type=int, default=4, help="warm start: network grid coarsening factor")
+    ap.add_argument("--ws-pool", type=int, default=8, help="warm start: network grid coarsening factor")
+    ap.add_argument("--ws-label-rtol", type=float, default=1e-6, help="warm start: label solve tolerance (--leg)")
+    ap.add_argument("--ws-reps", type=int, default=2, help="warm start: alternated timed solves per start (--leg)")
     ap.add_argument("--ws-train-default", type=int, default=2048,
                     help="warm start inside the default run: training pairs (bounded so the run ends in minutes)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start leg of the default run")
@@ -528,8 +559,16 @@ def main():
         from paper_2204_02064_gb300 import api
         ctx = api.Context(0)
         print(json.dumps({"leg": "warmstart", **warmstart_leg(api, torch, ctx, ntrain=args.ws_train,
-                                                                epochs=args.ws_epochs, pool=args.ws_pool)}),
+                                                                epochs=args.ws_epochs, pool=args.ws_pool,
+                                                                label_rtol=args.ws_label_rtol,
+                                                                reps=args.ws_reps)}),
               flush=True)
+        return 0
+    if args.leg == "cg":
+        import torch
+        from paper_2204_02064_gb300 import api
+        ctx = api.Context(0)
+        print(json.dumps({"leg": "cg", **cg_leg(api, torch, ctx, 10)}), flush=True)
         return 0
     if args.profile:
         return profile_case(args.profile)

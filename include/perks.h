@@ -104,6 +104,17 @@ perks_status perks_barrier_benchmark(perks_context *ctx, int32_t blocks, int32_t
  * Errors: INVALID_ARG, CUDA. */
 perks_status perks_fp64_fma_benchmark(perks_context *ctx, int32_t iterations, double *tflops);
 
+/* Random-gather throughput (a measurement aid, not in the paper): times one
+ * launch (after a warm-up launch that also brings the vector into L2) of 4
+ * blocks of 256 threads per SM, each thread issuing `iterations` x 8
+ * independent cache-global loads of elem_bytes (4 or 8) at pseudo-random
+ * positions of a vector of 2^log2_elems elements (10..28), and returns the
+ * loads per second: the ceiling of an SpMV whose column indices are
+ * scattered over a vector that L2 holds (one 32-byte sector per gathered
+ * value).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+perks_status perks_gather_benchmark(perks_context *ctx, int32_t log2_elems, int32_t elem_bytes,
+                                    int32_t iterations, double *gathers_per_s);
+
 /* Device facts used by planners and reports: SM count, opt-in shared memory
  * per block (bytes), L2 size (bytes).  Any out pointer may be NULL. */
 perks_status perks_context_info(const perks_context *ctx, int32_t *sm_count,

@@ -132,6 +132,7 @@ def _declare(lib):
         "perks_stencil_run_noalloc": ([ctypes.POINTER(StencilDesc), P, P, i64, P, i32], i32),
         "perks_fp64_fma_benchmark": ([P, i32, ctypes.POINTER(f64)], i32),
         "perks_batch_set_kernel": ([P, i32, i32], i32),
+        "perks_gather_benchmark": ([P, i32, i32, i32, ctypes.POINTER(f64)], i32),
         "perks_op_set_spmv": ([P, i32], i32),
         "perks_op_set_vector_cache": ([P, i32], i32),
         "perks_op_vector_cache_active": ([P], i32),
@@ -252,6 +253,14 @@ class Context:
         """Measured FP64 pipe throughput in TFLOP/s (independent FMA chains on every SM)."""
         t = ctypes.c_double()
         self.check(self._lib.perks_fp64_fma_benchmark(self.handle, int(iterations), ctypes.byref(t)))
+        return t.value
+
+    def gather_benchmark(self, log2_elems: int = 20, iterations: int = 2000, elem_bytes: int = 8) -> float:
+        """Random gathers of elem_bytes (4 or 8) per second from an L2-resident
+        vector of 2^log2_elems elements."""
+        t = ctypes.c_double()
+        self.check(self._lib.perks_gather_benchmark(self.handle, int(log2_elems), int(elem_bytes), int(iterations),
+                                                    ctypes.byref(t)))
         return t.value
 
     def set_barrier_timeout(self, ns: int):

@@ -77,7 +77,66 @@ __global__ void __launch_bounds__(256) fp64_fma_kernel(double *out, int iters, d
     out[blockIdx.x * blockDim.x + threadIdx.x] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
 }
 
+// Random gathers from an L2-resident vector (cache-global loads, as the
+// row-vector SpMV issues them): eight independent linear-congruential index
+// streams per thread keep loads in flight; the sums are written out.
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(const T *__restrict__ x, unsigned mask, int iters, T *out) {
+    unsigned h[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 40503u * (k + 1);
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            h[k] = h[k] * 1664525u + 1013904223u;
+            acc[k] += __ldcg(x + ((h[k] >> 7) & mask));
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
 }  // namespace
+
+extern "C" perks_status perks_gather_benchmark(perks_context *ctx, int32_t log2_elems, int32_t elem_bytes,
+                                               int32_t iterations, double *gathers_per_s) {
+    if (!ctx) return PERKS_ERR_INVALID_ARG;
+    if (log2_elems < 10 || log2_elems > 28 || (elem_bytes != 4 && elem_bytes != 8) || iterations < 1 ||
+        !gathers_per_s)
+        return fail(ctx, PERKS_ERR_INVALID_ARG, "gather_benchmark: bad arguments");
+    perks_status rc = use_device(ctx);
+    if (rc) return rc;
+    const int threads = 256, blocks = 4 * ctx->sm_count;
+    const size_t n = (size_t)1 << log2_elems;
+    void *x = nullptr, *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&x, n * elem_bytes);
+    if (e == cudaSuccess) e = cudaMemset(x, 0, n * elem_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)elem_bytes * threads * blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up (and fills L2)
+        e = cudaEventRecord(e0);
+        if (elem_bytes == 8)
+            gather_kernel<double><<<blocks, threads>>>((const double *)x, (unsigned)(n - 1), iterations,
+                                                       (double *)out);
+        else
+            gather_kernel<float><<<blocks, threads>>>((const float *)x, (unsigned)(n - 1), iterations,
+                                                      (float *)out);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (x) cudaFree(x);
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather_benchmark");
+    *gathers_per_s = 8.0 * (double)iterations * threads * blocks / (ms * 1e-3);
+    return PERKS_OK;
+}
 
 extern "C" perks_status perks_fp64_fma_benchmark(perks_context *ctx, int32_t iterations, double *tflops) {
     if (!ctx) return PERKS_ERR_INVALID_ARG;

@@ -156,10 +156,36 @@ def _solve(ctx, k, f, x0=None, rtol=1e-8):
     return x, res
 
 
+def _timed_solve(ctx, k, f, net=None, rtol=1e-8):
+    """Wall time (CUDA events) of one batched solve to rtol, the network's
+    inference included when `net` gives the start; returns (ms, stats)."""
+    from paper_2204_02064_gb300 import api
+    P = api.Poisson(ctx, k)
+    x = torch.zeros_like(f)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    if net is not None:
+        net.predict(k, f, x)
+    P.solve(f, x, rtol=rtol, stats=False)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    x2 = torch.zeros_like(f)
+    if net is not None:
+        net.predict(k, f, x2)
+    res = P.solve(f, x2, rtol=rtol)
+    P.close()
+    return ms, res
+
+
 def test_trained_net_gains_over_zero_start(ctx):
     """Train on solver-generated pairs, then solve held-out problems to 1e-8
     from zero and from the network's prediction: both reach the tolerance
-    (CG decides), and the warm start needs fewer iterations."""
+    (CG decides), and the warm start needs fewer iterations and less wall
+    time, its inference included (medians of five alternated timed solves
+    of each start)."""
     from paper_2204_02064_gb300 import api
     n, ntrain, ntest = 64, 512, 64
     k, f = inputs.poisson_problems_device(n, ntrain + ntest, seed=inputs.SEED_POISSON, ell=4.0)
@@ -177,6 +203,14 @@ def test_trained_net_gains_over_zero_start(ctx):
     print("zero-start mean iterations %.1f, warm-start %.1f, losses %s"
           % (zero["mean_iterations"], warm["mean_iterations"], losses[[0, -1]]))
     assert warm["mean_iterations"] < zero["mean_iterations"]
+    t_zero, t_warm = [], []
+    for rep in range(5):
+        for which in ((0, 1) if rep % 2 == 0 else (1, 0)):
+            ms, r = _timed_solve(ctx, kt, ft, net if which else None)
+            assert r["max_true_rel_residual"] <= 1e-8
+            (t_warm if which else t_zero).append(ms)
+    print("zero-start ms %s, warm-start ms %s" % (sorted(t_zero), sorted(t_warm)))
+    assert np.median(t_warm) < np.median(t_zero)
 
 
 def _pool(a, F):
