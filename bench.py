@@ -737,7 +737,7 @@ def main():
                                                        "smem_cache_planes", "cached_cells",
                                                        "halo_cells_per_step")},
                                 "kernel": kernel_name(desc), "planes_per_sync": desc["planes_per_sync"],
-                                "autotuned": True}},
+                                "balanced": bool(tuned.get("balanced")), "autotuned": True}},
             "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": tflops / fp64_peak, "traffic": traffic,
                          "peak_kind": "measured: fp64 FMA throughput of this GPU (perks_fp64_fma_benchmark, "
@@ -894,9 +894,13 @@ def kernel_signature(desc, tuned):
     body = ("cache-free body" if desc["reg_cache_planes"] == 0 and desc["smem_cache_planes"] == 0
             else "cached body (%d register + %d shared-memory planes)" % (desc["reg_cache_planes"],
                                                                           desc["smem_cache_planes"]))
-    return ("perks_stencil_vec_kernel<double, 3d7pt, NT=%d, V=2, ZR=%d, D=%d, P=%d> (plane streaming, %s), "
-            "tiles %dx%dx%d" % (desc["threads_per_block"], desc["reg_cache_planes"], desc["prefetch_planes"],
-                                desc["planes_per_sync"], body, desc["tiles_x"], desc["tiles_y"], desc["tiles_z"]))
+    split = ("tile columns %dx%d in balanced shares over %d blocks" % (desc["tiles_x"], desc["tiles_y"],
+                                                                       desc["grid_blocks"])
+             if tuned and tuned.get("balanced") else
+             "tiles %dx%dx%d" % (desc["tiles_x"], desc["tiles_y"], desc["tiles_z"]))
+    return ("perks_stencil_vec_kernel<double, 3d7pt, NT=%d, V=2, ZR=%d, D=%d, P=%d> (plane streaming, %s), %s"
+            % (desc["threads_per_block"], desc["reg_cache_planes"], desc["prefetch_planes"],
+               desc["planes_per_sync"], body, split))
 
 
 def desc_signature(desc):

@@ -164,6 +164,14 @@ typedef struct {
                                            plane-streaming kernel's two-blocks-per-SM
                                            instantiations where they exist (fp64 3d7pt,
                                            cache-free body) */
+    int32_t balanced;                   /* plane streaming with no caches (reg_cache = 0,
+                                           smem_cache_planes = 0): 1 = the tiles_x x tiles_y
+                                           tile columns are laid end to end (each column all
+                                           its planes in z) and cut into equal contiguous
+                                           shares, one per co-resident block, so every block
+                                           gets the same number of planes whatever the block
+                                           count (a share may end one column and start the
+                                           next); tiles_z is ignored.  0 = one tile per block */
 } perks_stencil_plan;
 
 /* What a run did; filled by perks_stencil_run when asked. */

@@ -50,7 +50,8 @@ class StencilDesc(ctypes.Structure):
 class StencilPlan(ctypes.Structure):
     _fields_ = [("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
                 ("tiles_z", ctypes.c_int32), ("smem_cache_planes", ctypes.c_int32),
-                ("reg_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("reg_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+                ("balanced", ctypes.c_int32)]
 
 
 class RunStats(ctypes.Structure):
@@ -360,7 +361,7 @@ class Stencil:
 
     def set_plan(self, tiles=(0, 0, 0), smem_cache_planes: int = -1, reg_cache: int = 1,
                  scalar: bool = False, planes_per_barrier: int = 0, kernel: int = KERNEL_AUTO,
-                 threads: int = 0, rows: int = 0):
+                 threads: int = 0, rows: int = 0, balanced: bool = False):
         """Plan override; ``scalar`` selects the one-cell-per-thread kernel
         instead of the 16-byte-vector kernel; ``planes_per_barrier`` (2 or 4,
         0 = automatic) picks how many planes the vector kernel computes
@@ -368,7 +369,9 @@ class Stencil:
         resident-tile kernel (``tiles`` and ``threads`` 256/512 apply to
         it, 0 = automatic), KERNEL_STREAMING / KERNEL_AUTO the plane-streaming
         kernel; ``rows`` (1 or 2, 0 = automatic) is the resident kernel's
-        rows per thread."""
+        rows per thread; ``balanced`` (cache-free plane streaming only) cuts
+        the tile columns' planes into equal shares, one per co-resident
+        block, instead of one tile per block."""
         p = StencilPlan()
         p.tiles_x, p.tiles_y, p.tiles_z = [int(t) for t in tiles]
         p.smem_cache_planes = int(smem_cache_planes)
@@ -377,6 +380,7 @@ class Stencil:
         p.reserved[1] = int(planes_per_barrier)
         p.reserved[2] = int(kernel)
         p.reserved[3] = int(threads)
+        p.balanced = 1 if balanced else 0
         self.ctx.check(self._lib.perks_stencil_set_plan(self.handle, ctypes.byref(p)))
 
     def autotune(self, variant: int = PERSISTENT, probe_steps: int = 10, stream=None) -> dict:
@@ -390,7 +394,7 @@ class Stencil:
                 "smem_cache_planes": p.smem_cache_planes, "planes_per_barrier": p.reserved[1],
                 "kernel": KERNEL_NAMES.get(p.reserved[2], "streaming"), "threads": p.reserved[3],
                 "rows": p.reg_cache if p.reserved[2] == KERNEL_RESIDENT else 0,
-                "ms_per_step": ms.value}
+                "balanced": bool(p.balanced), "ms_per_step": ms.value}
 
     def set_trace(self, steps: int):
         """Record per-block start/end times of the first ``steps`` steps of the

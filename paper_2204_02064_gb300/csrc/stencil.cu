@@ -159,6 +159,7 @@ struct Plan {
     int zs = 0;
     long long smem = 0;
     int blocks = 0;
+    bool balanced = false;     // cache-free body: equal shares of the ntx x nty columns' planes per block
     long long cached_cells = 0;
     long long halo_cells = 0;  // per step
     // resident-tile kernel (the whole tile in shared memory): tiles ntx x nty x ntz of
@@ -367,6 +368,10 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
                     "no %s kernel for this dtype/shape/extent (bf16 needs nx divisible by 8)",
                     per_step ? "per-step" : "persistent");
     KernelEntry &k = *kp;
+    const bool balanced = st->has_plan && st->plan.balanced != 0;
+    if (balanced && !(k.per_step && k.v > 1))
+        return fail(ctx, PERKS_ERR_UNSUPPORTED,
+                    "balanced shares need the cache-free vector body (reg_cache = 0, smem_cache_planes = 0)");
     int smem_budget = 0;
     {
         perks_status rc = smem_optin(ctx, (const void *)k.fn, &smem_budget);
@@ -414,14 +419,18 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
             const long long ring_bytes = (long long)S * PW * PH * es;
             if (ring_bytes > smem_budget) continue;
             int ntz;
-            if (st->has_plan && st->plan.tiles_z > 0) ntz = st->plan.tiles_z;
+            if (balanced) ntz = 1;
+            else if (st->has_plan && st->plan.tiles_z > 0) ntz = st->plan.tiles_z;
             else ntz = std::min(Z / std::max(RZ, 1), maxG / (ntx * nty));
             if (ntz < 1 || (long long)ntx * nty * ntz > maxG) continue;
             if (Z / ntz < std::max(RZ, 1)) continue;
-            const int tzmax = ceil_div(Z, ntz);
+            // planes per block: a tile's depth, or a balanced share (which may
+            // be cut once more where it crosses into the next column)
+            const int tzmax = balanced ? (int)(((long long)ntx * nty * Z + maxG - 1) / maxG) : ceil_div(Z, ntz);
+            if (balanced && tzmax < 4 * std::max(RZ, 1)) continue;  // shares too thin for their z-halos
             const double vol = (double)txmax * tymax * tzmax;
             const double cost = vol * (1.0 + 2.0 * RX / txmax + (RY ? 2.0 * RY / tymax : 0.0) +
-                                       2.0 * RZ / tzmax) +
+                                       (balanced ? 4.0 : 2.0) * RZ / tzmax) +
                                 (txmax < 32 ? vol * 0.25 : 0.0);
             if (cost < best) {
                 best = cost;
@@ -439,7 +448,8 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
     bp.k = &k;
     bp.plane = bp.PW * bp.PH;
     bp.ncol = bp.txmax * bp.tymax;
-    bp.blocks = bp.ntx * bp.nty * bp.ntz;
+    bp.balanced = balanced;
+    bp.blocks = balanced ? maxG : bp.ntx * bp.nty * bp.ntz;
     const long long ring_bytes = (long long)S * bp.plane * es;
     long long zs = (smem_budget - ring_bytes) / ((long long)bp.ncol * es);
     zs = std::min<long long>(zs, std::max(0, bp.tzmax - k.zr));
@@ -450,7 +460,7 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
 
     // cached cells and halo cells per step, tile by tile
     long long cached = 0, halo = 0;
-    for (int t = 0; t < bp.blocks; ++t) {
+    for (int t = 0; t < bp.ntx * bp.nty * bp.ntz; ++t) {
         const int ti = t % bp.ntx, tj = (t / bp.ntx) % bp.nty, tk = t / (bp.ntx * bp.nty);
         int x0, tx, y0, ty, z0, tz;
         split_axis(XU, bp.ntx, ti, x0, tx);
@@ -467,6 +477,14 @@ perks_status make_plan(perks_stencil *st, Plan &pl, bool per_step = false) {
         const long long wy = (long long)nfy * RY * tx * zc;
         const long long wz = (long long)nfz * RZ * tx * ty;
         halo += 2 * (wx + wy + wz);
+    }
+    if (balanced) {
+        // z-halos at the share boundaries that fall inside a column
+        const long long L = (long long)bp.ntx * bp.nty * Z;
+        for (int b = 1; b < bp.blocks; ++b) {
+            const long long cut = L * b / bp.blocks;
+            if (cut % Z != 0) halo += 2LL * 2 * RZ * bp.txmax * bp.tymax;
+        }
     }
     bp.cached_cells = cached;
     bp.halo_cells = halo;
@@ -646,6 +664,7 @@ void fill_args(const perks_stencil *st, const Plan &pl, long long steps, Persist
     for (int i = 0; i < kMaxKernelPoints; ++i) { a.w[i] = st->kw[i]; a.wf[i] = (float)st->kw[i]; }
     a.face_plane = (long long)pl.tzmax * pl.tymax;
     a.faces_cached_only = 1;
+    a.lin_cols = pl.balanced ? pl.ntx * pl.nty : 0;
 }
 
 perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, Plan &pl) {
@@ -1033,14 +1052,17 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
             }
             ctx->last_error = saved_msg;
         }
-    // plane-streaming kernels compiled with 256 threads (two blocks per SM): the model's tiling
+    // plane-streaming kernels compiled with 256 threads (two blocks per SM): the model's tiling,
+    // one tile per block and in balanced shares
     if (!per_step)
-        for (int P : {2, 4}) {
+        for (int cand = 0; cand < 4; ++cand) {
+            const int P = cand & 1 ? 4 : 2;
             perks_stencil_plan p{};
             p.smem_cache_planes = 0;
             p.reg_cache = 0;
             p.reserved[1] = P;
             p.reserved[3] = 256;
+            p.balanced = cand >= 2;
             st->plan = p;
             st->has_plan = true;
             Plan probe;
@@ -1059,13 +1081,15 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
     for (const TileCand &c : tile_candidates(st, per_step, 6))
         if (!(c.ntx == base.ntx && c.nty == base.nty && c.ntz == base.ntz)) tilings.push_back({c.ntx, c.nty, c.ntz});
     for (const auto &t : tilings)
-        for (int cache = per_step ? 0 : 2; cache >= 0; --cache)  // 2: registers + smem, 1: smem, 0: none
-            for (int P : {2, 4}) {
+        for (int cache = per_step ? 0 : 2; cache >= -1; --cache)  // 2: registers + smem, 1: smem, 0: none,
+            for (int P : {2, 4}) {                                  // -1: none, balanced shares
                 perks_stencil_plan p{};
-                p.tiles_x = t[0]; p.tiles_y = t[1]; p.tiles_z = t[2];
-                p.smem_cache_planes = cache == 0 ? 0 : -1;
+                p.tiles_x = t[0]; p.tiles_y = t[1]; p.tiles_z = cache < 0 ? 1 : t[2];
+                p.smem_cache_planes = cache <= 0 ? 0 : -1;
                 p.reg_cache = cache == 2 ? 1 : 0;
                 p.reserved[1] = P;
+                p.balanced = cache < 0;
+                if (cache < 0 && t[2] == 1) continue;  // one tile per column already: nothing to balance
                 plans.push_back(p);
             }
     // save the field; every trial starts from it

@@ -123,6 +123,10 @@ struct PersistentArgs {
     // field holds every uncached plane, so neighbours read its x-halo there);
     // requires every tile of a z-layer to cache the same planes
     int faces_cached_only;
+    // > 0 (cache-free plane-streaming body only): the lin_cols tile columns
+    // (tiles ntx x nty, each all Z planes) laid end to end are cut into
+    // gridDim.x equal contiguous shares of column-planes, one per block
+    int lin_cols;
 };
 
 __device__ __forceinline__ void trace_mark(const PersistentArgs &a, long long k, int which) {

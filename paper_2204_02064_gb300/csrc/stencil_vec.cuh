@@ -636,7 +636,29 @@ __global__ void __launch_bounds__(NT, MINB) perks_stencil_vec_kernel(const __gri
     for (long long k = 0; k < a.steps; ++k) {
         const bool last = (k + 1 == a.steps);
         if (!PER_STEP) trace_mark(a, k, 0);
-        sb = vec_step<T, SH, V, ZR, D, PER_STEP, P>(a, tp, k, last, sb, ring, smc, regc);
+        if (PER_STEP && a.lin_cols > 0) {
+            // balanced shares: this block's run of column-planes [s0, s1), as
+            // pieces of consecutive tile columns; halos come from the field,
+            // so any piece of a column is computed like a tile of its own
+            const long long L = (long long)a.lin_cols * a.Z;
+            long long s0 = L * blockIdx.x / gridDim.x;
+            const long long s1 = L * (blockIdx.x + 1) / gridDim.x;
+            while (s0 < s1) {
+                const int c = (int)(s0 / a.Z);
+                const long long cz = (long long)c * a.Z;
+                VecPlan sp = make_vec_plan<SH, V, PER_STEP>(a, c);
+                sp.z0 = (int)(s0 - cz);
+                sp.tz = (int)(min(s1, cz + a.Z) - s0);
+                sb = vec_step<T, SH, V, ZR, D, PER_STEP, P>(a, sp, k, last, sb, ring, smc, regc);
+                s0 = cz + a.Z;
+                if (s0 < s1) {  // the next piece's prologue refills ring slots still being read
+                    cp_async_wait_all();
+                    __syncthreads();
+                }
+            }
+        } else {
+            sb = vec_step<T, SH, V, ZR, D, PER_STEP, P>(a, tp, k, last, sb, ring, smc, regc);
+        }
         if (!PER_STEP) trace_mark(a, k, 1);
         if (!last) {
             if (!grid_barrier(a.bar, gridDim.x, epoch, a.err, a.timeout_ns)) break;

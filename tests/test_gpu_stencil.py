@@ -333,6 +333,20 @@ def test_full_size_sampled_oracle_on_autotuned_plan(ctx, oracle, L, dtype):
     picks = [(0, 0, 0), (L - 1, L - 1, L - 1), (0, L // 2, L - 1), (L // 2, 0, L // 3), (L // 2, L // 2, L // 2),
              (tz, ty, tx), (tz - 1, ty - 1, tx - 1), (tz, 5, 7), (3, ty, L - 4), (L - 2, 2 * ty - 1, tx),
              (2 * tz - 1, L // 3, 2 * tx - 1), (L // 4, 3 * L // 4, 1)]
+    if plan.get("balanced"):
+        # cells on both sides of the share boundaries that fall inside a column
+        ntx, nty, G = d["tiles_x"], d["tiles_y"], d["grid_blocks"]
+        V = {"f64": 2, "f32": 4, "bf16": 8}[dtype]
+
+        def start(n, parts, i):
+            base, rem = n // parts, n % parts
+            return i * base + min(i, rem)
+        total = ntx * nty * L
+        for b in (1, G // 3, G // 2, G - 1):
+            cut = total * b // G
+            col, z = cut // L, cut % L
+            x0, y0 = start(L // V, ntx, col % ntx) * V, start(L, nty, col // ntx)
+            picks += [(z, y0, x0), (max(z - 1, 0), y0 + 1, x0 + 1)]
     for c in picks:
         c = tuple(min(max(v, 0), L - 1) for v in c)
         ref = _window_oracle(oracle, base, c, steps, offs, w, dtype)
