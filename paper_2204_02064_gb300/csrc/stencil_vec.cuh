@@ -347,8 +347,20 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
                 });
             }
             // x-neighbour cells: from the adjacent lanes' vectors of the same
-            // row by warp shuffles; lanes at a row or warp edge read the ring
+            // row by warp shuffles; lanes at a row or warp edge read the ring.
+            // fp64 reads them from the ring in every lane: one 8-byte load per
+            // side instead of two 32-bit shuffles and a fallback load.
             const int lane = threadIdx.x & 31;
+            if constexpr (std::is_same<T, double>::value) {
+                if constexpr (left) static_for<0, R>([&](auto JI) {
+                    constexpr int j = decltype(JI)::value;
+                    seg[r][j] = rp[j - R];
+                });
+                if constexpr (right) static_for<0, R>([&](auto JI) {
+                    constexpr int j = decltype(JI)::value;
+                    seg[r][R + V + j] = rp[V + j];
+                });
+            } else {
             if constexpr (left) {
                 static_for<0, R>([&](auto JI) {
                     constexpr int j = decltype(JI)::value;      // cell at offset j - R
@@ -369,6 +381,7 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
                     if (tp.rowpos + fwd < tp.nvx && lane + fwd < 32) seg[r][R + V + j] = v;
                     else seg[r][R + V + j] = to_acc(rp[V + j]);
                 });
+            }
             }
         });
         VT out;
