@@ -362,8 +362,13 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
 // multiply-add per nonzero; the sub-warp sums by shuffles.  On GB300 this
 // costs ~8 instructions per nonzero against ~20 for the thread-level merge
 // walk; the block-level merge-path partition still balances the blocks.
-constexpr int kSub = 4;
-constexpr int kRowsPer = 4;
+// Measured on GB300 (n = 2^20, 36.7 M nonzeros): 8 lanes per row; fp64
+// one row per sub-warp with 8 steps of loads in flight, fp32 two rows with 4
+// steps (the lone fp64 SpMV 218 -> 179 us against the first, unpipelined
+// 4-lane layout).
+constexpr int kSub = 8;
+template <typename V> __host__ __device__ constexpr int rows_per() { return sizeof(V) == 8 ? 1 : 2; }
+template <typename V> __host__ __device__ constexpr int steps_per() { return sizeof(V) == 8 ? 8 : 4; }  // loads in flight per row
 
 template <typename V>
 __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__restrict__ gval,
@@ -373,6 +378,7 @@ __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__
     const int sub = threadIdx.x / kSub;
     const int nsub = blockDim.x / kSub;
     const unsigned mask = 0xffffffffu;
+    constexpr int kRowsPer = rows_per<V>(), kU = steps_per<V>();
     double dot = 0.0;
     const int stride = nsub * kRowsPer;
     for (int base = sl.r0; base < sl.r1; base += stride) {
@@ -388,12 +394,31 @@ __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__
             acc[k] = V(0);
             longest = max(longest, je[k] - jb[k] + lane);
         }
-        for (int u = 0; u < longest; u += kSub) {
+        // kU steps of every row at a time: all their column indices and
+        // values are loaded first, then all the gathers are issued, then the
+        // FMAs run (each row's terms still in order), so one pass waits for
+        // one HBM load and one L2 gather instead of kU of each
+        for (int u = 0; u < longest; u += kSub * kU) {
+            int cj[kU][kRowsPer];
+            V vv[kU][kRowsPer], xv[kU][kRowsPer];
 #pragma unroll
-            for (int k = 0; k < kRowsPer; ++k) {
-                const int j = jb[k] + u;
-                if (j < je[k]) acc[k] = fma(__ldcs(gval + j), __ldcg(vin + __ldcs(a.col + j)), acc[k]);
-            }
+            for (int q = 0; q < kU; ++q)
+#pragma unroll
+                for (int k = 0; k < kRowsPer; ++k) {
+                    const int j = jb[k] + u + q * kSub;
+                    const bool in = j < je[k];
+                    cj[q][k] = in ? __ldcs(a.col + j) : -1;
+                    vv[q][k] = in ? __ldcs(gval + j) : V(0);
+                }
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+#pragma unroll
+                for (int k = 0; k < kRowsPer; ++k) xv[q][k] = cj[q][k] >= 0 ? __ldcg(vin + cj[q][k]) : V(0);
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+#pragma unroll
+                for (int k = 0; k < kRowsPer; ++k)
+                    if (cj[q][k] >= 0) acc[k] = fma(vv[q][k], xv[q][k], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < kRowsPer; ++k) {
