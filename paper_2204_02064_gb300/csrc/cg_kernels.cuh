@@ -362,23 +362,61 @@ __device__ double spmv_block(const CgArgs &a, const CgSmem &s, const CgSlice &sl
 // multiply-add per nonzero; the sub-warp sums by shuffles.  On GB300 this
 // costs ~8 instructions per nonzero against ~20 for the thread-level merge
 // walk; the block-level merge-path partition still balances the blocks.
-// Measured on GB300 (n = 2^20, 36.7 M nonzeros): 8 lanes per row; fp64
-// one row per sub-warp with 8 steps of loads in flight, fp32 two rows with 4
-// steps (the lone fp64 SpMV 218 -> 179 us against the first, unpipelined
-// 4-lane layout).
+// A DFMA costs a whole warp issue on GB300's FP64 pipe (2 lanes per clock
+// per SM) however many lanes it has active, so the layout keeps warp
+// instructions dense: 8 lanes per row and two rows per sub-warp, the steps
+// a warp runs end at its longest row (full passes of kU steps, then passes of
+// 4, 2 and 1 for the remainder), and the two rows' partial sums are reduced together (one exchange hands each half of
+// the sub-warp one row, so 3 additions cover both rows instead of 6).
+// Measured (n = 2^20, 36.7 M nonzeros): the lone fp64 SpMV 218 us with the
+// first, unpipelined 4-lane layout; 179 us with 8 lanes, one row and 8
+// steps of loads in flight.
 constexpr int kSub = 8;
-template <typename V> __host__ __device__ constexpr int rows_per() { return sizeof(V) == 8 ? 1 : 2; }
-template <typename V> __host__ __device__ constexpr int steps_per() { return sizeof(V) == 8 ? 8 : 4; }  // loads in flight per row
+constexpr int kRowsPer = 2;
+// steps of both rows whose loads are in flight together in a full pass
+// (fp64 4, fp32 6: within the persistent kernel's 64 registers)
+template <typename V> __host__ __device__ constexpr int full_pass_steps() { return sizeof(V) == 8 ? 4 : 6; }
+
+// UU steps of both rows of a sub-warp: all their column indices and values
+// are loaded first, then all the gathers are issued, then the FMAs run (each
+// row's terms still in order), so the pass waits for one HBM load and one L2
+// gather instead of UU of each.
+template <int UU, typename V>
+__device__ __forceinline__ void spmv_pass(const int *__restrict__ col, const V *__restrict__ gval,
+                                          const V *__restrict__ vin, const int (&jb)[kRowsPer],
+                                          const int (&je)[kRowsPer], int u, V (&acc)[kRowsPer]) {
+    int cj[UU][kRowsPer];
+    V vv[UU][kRowsPer], xv[UU][kRowsPer];
+#pragma unroll
+    for (int q = 0; q < UU; ++q)
+#pragma unroll
+        for (int k = 0; k < kRowsPer; ++k) {
+            const int j = jb[k] + u + q * kSub;
+            const bool in = j < je[k];
+            cj[q][k] = in ? __ldcs(col + j) : -1;
+            vv[q][k] = in ? __ldcs(gval + j) : V(0);
+        }
+#pragma unroll
+    for (int q = 0; q < UU; ++q)
+#pragma unroll
+        for (int k = 0; k < kRowsPer; ++k) xv[q][k] = cj[q][k] >= 0 ? __ldcg(vin + cj[q][k]) : V(0);
+#pragma unroll
+    for (int q = 0; q < UU; ++q)
+#pragma unroll
+        for (int k = 0; k < kRowsPer; ++k)
+            if (cj[q][k] >= 0) acc[k] = fma(vv[q][k], xv[q][k], acc[k]);
+}
 
 template <typename V>
 __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__restrict__ gval,
                                  const V *__restrict__ vin, V *__restrict__ vout, const V *dotv, double *red,
                                  V *vout_s) {
+    static_assert(kRowsPer == 2 && kSub == 8, "the reduction below pairs two rows over eight lanes");
+    constexpr int kU = full_pass_steps<V>();
     const int lane = threadIdx.x & (kSub - 1);
     const int sub = threadIdx.x / kSub;
     const int nsub = blockDim.x / kSub;
     const unsigned mask = 0xffffffffu;
-    constexpr int kRowsPer = rows_per<V>(), kU = steps_per<V>();
     double dot = 0.0;
     const int stride = nsub * kRowsPer;
     for (int base = sl.r0; base < sl.r1; base += stride) {
@@ -394,46 +432,35 @@ __device__ double spmv_block_vec(const CgArgs &a, const CgSlice &sl, const V *__
             acc[k] = V(0);
             longest = max(longest, je[k] - jb[k] + lane);
         }
-        // kU steps of every row at a time: all their column indices and
-        // values are loaded first, then all the gathers are issued, then the
-        // FMAs run (each row's terms still in order), so one pass waits for
-        // one HBM load and one L2 gather instead of kU of each
-        for (int u = 0; u < longest; u += kSub * kU) {
-            int cj[kU][kRowsPer];
-            V vv[kU][kRowsPer], xv[kU][kRowsPer];
-#pragma unroll
-            for (int q = 0; q < kU; ++q)
-#pragma unroll
-                for (int k = 0; k < kRowsPer; ++k) {
-                    const int j = jb[k] + u + q * kSub;
-                    const bool in = j < je[k];
-                    cj[q][k] = in ? __ldcs(a.col + j) : -1;
-                    vv[q][k] = in ? __ldcs(gval + j) : V(0);
-                }
-#pragma unroll
-            for (int q = 0; q < kU; ++q)
-#pragma unroll
-                for (int k = 0; k < kRowsPer; ++k) xv[q][k] = cj[q][k] >= 0 ? __ldcg(vin + cj[q][k]) : V(0);
-#pragma unroll
-            for (int q = 0; q < kU; ++q)
-#pragma unroll
-                for (int k = 0; k < kRowsPer; ++k)
-                    if (cj[q][k] >= 0) acc[k] = fma(vv[q][k], xv[q][k], acc[k]);
+        // steps any lane of this warp still needs (uniform across the warp)
+        const int wlong = __reduce_max_sync(mask, longest);
+        // full passes of kU steps, then the remainder in passes of 4, 2 and 1:
+        // no step issues FMAs that no lane of the warp needs
+        int u = 0;
+        for (; u + kSub * kU <= wlong; u += kSub * kU) spmv_pass<kU>(a.col, gval, vin, jb, je, u, acc);
+        if (kU > 4 && u + kSub * 4 <= wlong) {
+            spmv_pass<4>(a.col, gval, vin, jb, je, u, acc);
+            u += 4 * kSub;
         }
-#pragma unroll
-        for (int k = 0; k < kRowsPer; ++k) {
-#pragma unroll
-            for (int o = kSub / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(mask, acc[k], o, kSub);
+        if (kU > 2 && u + kSub * 2 <= wlong) {
+            spmv_pass<2>(a.col, gval, vin, jb, je, u, acc);
+            u += 2 * kSub;
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kRowsPer; ++k) {
-                const int r = row0 + k;
-                if (r < sl.r1) {
-                    if (vout_s) vout_s[r - sl.r0] = acc[k];  // the block's own rows, kept on chip
-                    else vout[r] = acc[k];
-                    if (dotv) dot = fma((double)dotv[r], (double)acc[k], dot);
-                }
+        for (; u < wlong; u += kSub) spmv_pass<1>(a.col, gval, vin, jb, je, u, acc);
+        // lanes 0-3 of the sub-warp keep row 0, lanes 4-7 row 1: each sends
+        // the other row's partial across and adds the one it receives, then
+        // the four lanes of each half sum their row
+        const bool hi = (lane & 4) != 0;
+        V v = hi ? acc[1] : acc[0];
+        v += __shfl_xor_sync(mask, hi ? acc[0] : acc[1], 4, kSub);
+        v += __shfl_xor_sync(mask, v, 2, kSub);
+        v += __shfl_xor_sync(mask, v, 1, kSub);
+        if ((lane & 3) == 0) {
+            const int r = row0 + (hi ? 1 : 0);
+            if (r < sl.r1) {
+                if (vout_s) vout_s[r - sl.r0] = v;  // the block's own rows, kept on chip
+                else vout[r] = v;
+                if (dotv) dot = fma((double)dotv[r], (double)v, dot);
             }
         }
     }
