@@ -665,6 +665,14 @@ void fill_args(const perks_stencil *st, const Plan &pl, long long steps, Persist
     a.face_plane = (long long)pl.tzmax * pl.tymax;
     a.faces_cached_only = 1;
     a.lin_cols = pl.balanced ? pl.ntx * pl.nty : 0;
+    a.iso = 0;
+    if (st->shape_id == SH_3D7 && st->desc.dtype == PERKS_F64) {
+        bool eq = true;
+        for (int i = 2; i < 7; ++i) eq = eq && st->kw[i] == st->kw[1];
+        a.iso = eq ? 1 : 0;
+        a.wc = st->kw[0];
+        a.wn = st->kw[1];
+    }
 }
 
 perks_status run_persistent(perks_stencil *st, long long steps, cudaStream_t s, Plan &pl) {

@@ -127,6 +127,11 @@ struct PersistentArgs {
     // (tiles ntx x nty, each all Z planes) laid end to end are cut into
     // gridDim.x equal contiguous shares of column-planes, one per block
     int lin_cols;
+    // 1: fp64 3d7pt whose six neighbour weights are equal (wn; centre wc):
+    // the cache-free body sums the neighbours and shares one pair sum per
+    // thread between consecutive planes (see vcompute_store)
+    int iso;
+    double wc, wn;
 };
 
 __device__ __forceinline__ void trace_mark(const PersistentArgs &a, long long k, int which) {
