@@ -1097,7 +1097,6 @@ extern "C" perks_status perks_stencil_autotune(perks_stencil *st, int32_t varian
                 p.reg_cache = cache == 2 ? 1 : 0;
                 p.reserved[1] = P;
                 p.balanced = cache < 0;
-                if (cache < 0 && t[2] == 1) continue;  // one tile per column already: nothing to balance
                 plans.push_back(p);
             }
     // save the field; every trial starts from it
