@@ -109,3 +109,27 @@ def test_balanced_equals_one_tile_per_block_bitwise(ctx):
     b, _ = _run(ctx, "3d7pt", src, 20, dict(tiles=(2, 4, 3), smem_cache_planes=0, reg_cache=0,
                                             planes_per_barrier=4, threads=256), 0, "f64")
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("balanced", [False, True])
+@pytest.mark.parametrize("threads,P", [(256, 2), (256, 4), (0, 2)])
+def test_fp64_3d7pt_unequal_neighbour_weights(ctx, oracle, threads, P, balanced):
+    """fp64 3d7pt whose neighbour weights differ takes the cache-free body's
+    table-order sum (equal weights take the neighbour-sum form with a pair
+    sum carried between planes); both agree with the oracle."""
+    from paper_2204_02064_gb300 import api
+    shape, steps = (203, 24, 40), 11
+    w = np.array([0.31, 0.07, 0.13, 0.09, 0.11, 0.12, 0.17])
+    f = inputs.stencil_field(shape, 45)
+    src = torch.from_numpy(f).cuda()
+    st = api.Stencil(ctx, shape, inputs.shape_offsets("3d7pt"), w)
+    st.set_plan(tiles=(2, 4, 0 if balanced else 3), smem_cache_planes=0, reg_cache=0, planes_per_barrier=P,
+                threads=threads, balanced=balanced)
+    st.set_field(src)
+    st.run(steps, stats=True)
+    out = torch.empty_like(src)
+    st.get_field(out)
+    torch.cuda.synchronize()
+    st.close()
+    ref = oracle.stencil_run(f, inputs.shape_offsets("3d7pt"), w, steps)
+    assert rel_err(out.cpu().numpy(), ref) <= 1e-12
