@@ -388,17 +388,50 @@ __device__ __forceinline__ void vcompute_store(const PersistentArgs &a, const Ve
         VT out;
         A accs[V];
         auto table_order = [&]() {
-            static_for<0, V>([&](auto JI) {
-                constexpr int j = decltype(JI)::value;
-                A acc = A(0);
+            if constexpr (std::is_same<A, float>::value && V % 2 == 0 && !SH::BOX && SH::R <= 2) {
+                // fp32 accumulation (stars of radius <= 2): a term with dx = 0 updates two cells with
+                // one packed fma (__ffma2_rn rounds each lane as fmaf does),
+                // an x-shifted term one cell at a time; every cell still adds
+                // its terms in table order from 0
+                float2 acc2[V / 2];
+#pragma unroll
+                for (int k = 0; k < V / 2; ++k) acc2[k] = make_float2(0.f, 0.f);
                 static_for<0, SH::NPTS>([&](auto II) {
                     constexpr int i = decltype(II)::value;
                     constexpr int r = RW::row_of(i);
-                    constexpr int col = R + j + SH::dx(i);
-                    acc = fma(ScalarOps<T>::w(a, i), seg[r][col], acc);
+                    constexpr int dx = SH::dx(i);
+                    const float w = ScalarOps<T>::w(a, i);
+                    if constexpr (dx == 0) {
+                        const float2 w2 = make_float2(w, w);
+#pragma unroll
+                        for (int k = 0; k < V / 2; ++k)
+                            acc2[k] = __ffma2_rn(w2, make_float2(seg[r][R + 2 * k], seg[r][R + 2 * k + 1]), acc2[k]);
+                    } else {
+                        static_for<0, V>([&](auto JI) {
+                            constexpr int j = decltype(JI)::value;
+                            if constexpr (j & 1) acc2[j / 2].y = fmaf(w, seg[r][R + j + dx], acc2[j / 2].y);
+                            else acc2[j / 2].x = fmaf(w, seg[r][R + j + dx], acc2[j / 2].x);
+                        });
+                    }
                 });
-                accs[j] = acc;
-            });
+#pragma unroll
+                for (int k = 0; k < V / 2; ++k) {
+                    accs[2 * k] = acc2[k].x;
+                    accs[2 * k + 1] = acc2[k].y;
+                }
+            } else {
+                static_for<0, V>([&](auto JI) {
+                    constexpr int j = decltype(JI)::value;
+                    A acc = A(0);
+                    static_for<0, SH::NPTS>([&](auto II) {
+                        constexpr int i = decltype(II)::value;
+                        constexpr int r = RW::row_of(i);
+                        constexpr int col = R + j + SH::dx(i);
+                        acc = fma(ScalarOps<T>::w(a, i), seg[r][col], acc);
+                    });
+                    accs[j] = acc;
+                });
+            }
         };
         if constexpr (std::is_same<T, double>::value && SH::NDIM == 3 && SH::R == 1 && !SH::BOX && V == 2 &&
                       PER_STEP) {
