@@ -228,8 +228,9 @@ perks_status perks_stencil_get_trace(perks_stencil *st, uint64_t *host, int64_t 
  * prologue and epilogue cancel -- the resident-tile kernel with 256 and 512
  * threads and 1 and 2 rows per thread where the domain fits, and the model's
  * own tiling and up to six tilings ranked by tz * (1 + halo fraction), each
- * with registers + shared memory, shared memory only or no cache, and with 2
- * or 4 planes per block barrier -- restores the field, installs the fastest plan (as
+ * with registers + shared memory, shared memory only, no cache, or no cache
+ * in balanced shares (perks_stencil_plan.balanced), and with 2 or 4 planes
+ * per block barrier -- restores the field, installs the fastest plan (as
  * perks_stencil_set_plan would) and returns it with its time per step.
  * Synchronizes `stream`.  Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY,
  * CUDA, BARRIER_TIMEOUT. */
