@@ -352,7 +352,7 @@ perks_status forward(perks_warmnet *n, int nimg, int ny, int nx, const double *k
         // inner layers as implicit GEMMs on the tensor cores
         perks_status rc = set_smem(ctx, tc_conv32_kernel, tc_conv_smem());
         if (rc) return rc;
-        const long long ntiles = (long long)nimg * H * ((W + kTcPix - 1) / kTcPix);
+        const long long ntiles = (long long)nimg * (((long long)H * W + kTcPix - 1) / kTcPix);
         const int blocks = (int)std::min<long long>(ntiles, 2LL * ctx->sm_count);
         for (int l = 1; l <= 2; ++l)
             tc_conv32_kernel<<<blocks, kTcThreads, tc_conv_smem(), s>>>(

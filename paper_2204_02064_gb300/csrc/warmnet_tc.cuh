@@ -2,7 +2,9 @@
 // (NCHW), fp32 accumulation in tensor memory: the two inner layers of the
 // warm-start network, as an implicit GEMM.
 //
-// A tile is 128 consecutive pixels of one image row.  For each of the 9 taps
+// A tile is 128 consecutive pixels of one image in row-major order (it may
+// span several short rows, so no MMA row is wasted on grids narrower than 128
+// pixels; pixels past the image's end are zero rows).  For each of the 9 taps
 // the tile's input window (128 pixels x 32 channels, shifted by the tap's
 // offset times the dilation, zero outside the image) is the A operand
 // (M = 128, K = 32) and the tap's weights W[:, :, tap] the B operand
@@ -124,21 +126,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv32_kernel(const __nv_bfl
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = tc_idesc();
 
-    const int tiles_x = (W + kTcPix - 1) / kTcPix;
-    const long long ntiles = (long long)nimg * H * tiles_x;
     const long long plane = (long long)H * W;
+    const long long tiles_img = (plane + kTcPix - 1) / kTcPix;
+    const long long ntiles = (long long)nimg * tiles_img;
     unsigned parity = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int img = (int)(t / ((long long)H * tiles_x));
-        const int rem = (int)(t % ((long long)H * tiles_x));
-        const int y = rem / tiles_x, x0 = (rem % tiles_x) * kTcPix;
-        // A operands: pixel m = tid of the tile, all 32 channels, 9 taps
+        const int img = (int)(t / tiles_img);
+        const long long p0 = (t % tiles_img) * kTcPix;  // first pixel of the tile in its image
+        // A operands: pixel p0 + tid of the tile, all 32 channels, 9 taps
+        const long long pm = p0 + tid;
+        const bool valid = pm < plane;
+        const int y = valid ? (int)(pm / W) : 0, x = valid ? (int)(pm % W) : 0;
         const __nv_bfloat16 *inb = in + (long long)img * kTcC * plane;
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + (tap / 3 - 1) * dil, xx = x0 + tid + (tap % 3 - 1) * dil;
-            const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W && x0 + tid < W;
+            const int yy = y + (tap / 3 - 1) * dil, xx = x + (tap % 3 - 1) * dil;
+            const bool inside = valid && yy >= 0 && yy < H && xx >= 0 && xx < W;
             unsigned char *dst = sa + tap * kTcTapBytes;
 #pragma unroll
             for (int kg = 0; kg < 4; ++kg) {
@@ -179,9 +183,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv32_kernel(const __nv_bfl
               "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int px = x0 + warp * 32 + lane;
-        if (px < W) {
-            __nv_bfloat16 *ob = out + (long long)img * kTcC * plane + (long long)y * W + px;
+        const long long pe = p0 + warp * 32 + lane;  // TMEM lane = pixel of the tile
+        if (pe < plane) {
+            __nv_bfloat16 *ob = out + (long long)img * kTcC * plane + pe;
 #pragma unroll
             for (int c = 0; c < kTcC; ++c) {
                 const float v = fmaxf(__uint_as_float(r[c]) + bias[c], 0.f);
