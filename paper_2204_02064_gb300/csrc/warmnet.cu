@@ -1,7 +1,7 @@
 // Learned warm start for the variable-coefficient Poisson CG: a 4-layer,
 // 32-channel, 3x3 (dilated) convolutional network mapping (log k, f) -> u,
 // with hand-written forward, backward and Adam kernels.  Not in the paper;
-// plain CG to the same tolerance stays the judge of every solve.
+// plain CG to the same tolerance still decides when every solve is done.
 //
 // Layers: conv(2->C) ReLU, conv(C->C) ReLU, conv(C->C) ReLU, conv(C->1);
 // dilation per layer; zero padding.  Activations are stored in bf16 (or
