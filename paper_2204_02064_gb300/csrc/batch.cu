@@ -225,14 +225,48 @@ __device__ __forceinline__ void strip_item(const PersistentArgs &a, const StripI
                 fetch(z + R, win[(p + 2 * R) % W]);
                 VT o;
                 A acc[V];
+                if constexpr (std::is_same<A, float>::value && V % 2 == 0) {
+                    // fp32: a term whose x offset is even updates two cells
+                    // with one packed fma (__ffma2_rn rounds each lane as
+                    // fmaf does; the two cells sit in an aligned register
+                    // pair of the window row), an odd offset one cell at a
+                    // time; every cell adds its terms in table order from 0
+                    float2 acc2[V / 2];
 #pragma unroll
-                for (int q = 0; q < V; ++q) acc[q] = A(0);
-                static_for<0, SH::NPTS>([&](auto II) {
-                    constexpr int i = decltype(II)::value;
-                    constexpr int slot = (p + R + SH::dz(i)) % W;
+                    for (int q = 0; q < V / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+                    static_for<0, SH::NPTS>([&](auto II) {
+                        constexpr int i = decltype(II)::value;
+                        constexpr int slot = (p + R + SH::dz(i)) % W;
+                        constexpr int dx = SH::dx(i);
+                        if constexpr (dx % 2 == 0) {
+                            const float2 w2 = make_float2(w[i], w[i]);
 #pragma unroll
-                    for (int q = 0; q < V; ++q) acc[q] = fma(w[i], win[slot][2 + q + SH::dx(i)], acc[q]);
-                });
+                            for (int q = 0; q < V / 2; ++q)
+                                acc2[q] = __ffma2_rn(w2, make_float2(win[slot][2 + 2 * q + dx], win[slot][3 + 2 * q + dx]),
+                                                     acc2[q]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < V / 2; ++q) {
+                                acc2[q].x = fmaf(w[i], win[slot][2 + 2 * q + dx], acc2[q].x);
+                                acc2[q].y = fmaf(w[i], win[slot][3 + 2 * q + dx], acc2[q].y);
+                            }
+                        }
+                    });
+#pragma unroll
+                    for (int q = 0; q < V / 2; ++q) {
+                        acc[2 * q] = acc2[q].x;
+                        acc[2 * q + 1] = acc2[q].y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[q] = A(0);
+                    static_for<0, SH::NPTS>([&](auto II) {
+                        constexpr int i = decltype(II)::value;
+                        constexpr int slot = (p + R + SH::dz(i)) % W;
+#pragma unroll
+                        for (int q = 0; q < V; ++q) acc[q] = fma(w[i], win[slot][2 + q + SH::dx(i)], acc[q]);
+                    });
+                }
                 if constexpr (std::is_same<T, __nv_bfloat16>::value) {
                     __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&o);
 #pragma unroll
