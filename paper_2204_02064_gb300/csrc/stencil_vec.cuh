@@ -543,14 +543,14 @@ __device__ __forceinline__ void vplane_multi(const PersistentArgs &a, const VecP
     static_assert(P >= 1 && P <= D, "planes per barrier");
     cp_async_wait<D - P>();
     __syncthreads();
+    // each plane's fill follows its compute, spreading the copies over the
+    // group: the filled slots (slo + 2RZ + D + p, i.e. the group's last P
+    // slots before slo) are read by no plane of this group
     static_for<0, P>([&](auto PI) {
         constexpr int p = decltype(PI)::value;
         int s = slo + p;
         s = s >= S ? s - S : s;
         vcompute_store<T, SH, V, ZR, D, PER_STEP, STORE, P>(a, tp, z + p, s, last, ring, sp, smc, regc);
-    });
-    static_for<0, P>([&](auto PI) {
-        constexpr int p = decltype(PI)::value;
         vfill_next<T, SH, V, ZR, D, PER_STEP, FILL, P>(a, tp, z + p + RZ + D, slo + 2 * RZ + D + p, ring, sp, smc,
                                                       regc);
     });
