@@ -254,7 +254,12 @@ perks_status perks_stencil_set_field(perks_stencil *st, const void *src, int src
  *     halos through L2;
  *   PERKS_PER_STEP: one launch per step, every step reading and writing the
  *     whole field in HBM (the baseline PERKS is measured against).
- * Both give the same values up to rounding order.  With opt_out == NULL the
+ * Both give the same values up to rounding order: with fp32 / bf16 storage
+ * every kernel adds a cell's terms in table order by fp32 fused multiply-adds,
+ * so all plans and variants give the same bits; with fp64 the order can
+ * differ between kernel bodies (the cache-free 3d7pt body with six equal
+ * neighbour weights sums the neighbours, then applies the two weights).
+ * With opt_out == NULL the
  * call is asynchronous; device errors (BARRIER_TIMEOUT) then surface in
  * perks_stencil_check.  With opt_out != NULL the stream is synchronized and
  * opt_out filled.  Errors: INVALID_ARG, LAUNCH_TOO_LARGE, UNSUPPORTED,
