@@ -250,3 +250,18 @@ def test_poisson19_sine_mode_eigenvalue(oracle):
     steps = 7
     out = oracle.stencil_run(u, offs, w, steps)
     assert np.max(np.abs(out - lam ** steps * u)) <= 1e-13 * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("name,shape,steps", [("3d7pt", (17, 12, 9), 6), ("2d25pt", (31, 26), 5),
+                                              ("3d27pt", (9, 10, 11), 3)])
+def test_all_cores_build_is_bitwise_the_serial_oracle(oracle, name, shape, steps):
+    """The OpenMP build of the oracle (the all-cores CPU baseline) splits a
+    step's planes over threads but computes every cell as the serial build
+    does, so the two agree bit for bit."""
+    from paper_2204_02064_gb300 import inputs
+    f = inputs.stencil_field(shape, 47)
+    offs, w = inputs.shape_offsets(name), inputs.workload_weights(name, seed=5)
+    serial = oracle.stencil_run(f, offs, w, steps)
+    parallel, threads = oracle.stencil_run_all_cores(f, offs, w, steps)
+    assert threads >= 1
+    assert np.array_equal(serial, parallel)
